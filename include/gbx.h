@@ -1,0 +1,259 @@
+/*
+ * gbx.h -- C ABI of the GB300-native push-pull BFS library (libgbx.so).
+ *
+ * The library implements the hot path of "Implementing Push-Pull Efficiently
+ * in GraphBLAS" (Yang, Buluc, Owens, arXiv 1804.03327): the Boolean-semiring
+ * masked matvec f' = A^T f .* !v that every level of direction-optimized BFS
+ * runs (Algorithm 1), in its column-based "push" form (Eq 5, Algorithm 3),
+ * its row-based "pull" form restricted by the mask with early exit (Eq 4,
+ * Algorithm 2, Sections 5.2-5.3), and the per-level direction switch between
+ * them (Section 6.3).
+ *
+ * Conventions shared by every entry point:
+ *  - Errors: every call returns a gbx_status and never throws or aborts.  A
+ *    human-readable message for the last failing call on the calling thread is
+ *    returned by gbx_last_error().  No partial output is promised on error.
+ *  - Ownership: the library owns gbx_graph handles (and all memory reachable
+ *    from them) and frees them in gbx_graph_free.  The caller owns every
+ *    buffer it passes in (vectors, depth/parent arrays, edge lists) and keeps
+ *    it alive until the work that uses it has completed on the stream.
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *    default stream).  Device work is enqueued on it and the call returns
+ *    without synchronising unless its comment says otherwise.  Work on one
+ *    graph handle uses that handle's scratch memory, so calls on the same
+ *    graph must be ordered (one stream, or explicit events).
+ *  - Device pointers are plain CUDA device addresses (for example the
+ *    data_ptr() of a CUDA tensor); host pointers are ordinary addresses.
+ *  - Indices are int32; a graph holds fewer than 2^31 stored edges.
+ */
+#ifndef GBX_H
+#define GBX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes, modelled on GrB_Info of the GraphBLAS C API the paper targets. */
+typedef enum {
+    GBX_OK = 0,
+    GBX_ERR_INVALID_VALUE = 1,      /* a size, flag or descriptor field out of range */
+    GBX_ERR_INVALID_INDEX = 2,      /* a vertex id outside [0, n) */
+    GBX_ERR_DIMENSION_MISMATCH = 3, /* vector length differs from the graph's n */
+    GBX_ERR_OUT_OF_MEMORY = 4,      /* a device or host allocation failed */
+    GBX_ERR_NOT_SUPPORTED = 5,      /* e.g. a semiring other than GBX_LOR_LAND */
+    GBX_ERR_TIMEOUT = 6,            /* a bounded device-side wait ran out */
+    GBX_ERR_CUDA = 7,               /* a CUDA runtime call failed (message has details) */
+    GBX_ERR_OVERFLOW = 8,           /* a count exceeded its type (e.g. >= 2^31 edges) */
+    GBX_ERR_BUSY = 9,               /* a resource is in use */
+    GBX_ERR_NULL_POINTER = 10       /* a required pointer argument is NULL */
+} gbx_status;
+
+/* Message for the last failing call on this thread ("" if none).  The string is
+ * owned by the library and valid until the next call on this thread. */
+const char* gbx_last_error(void);
+/* Static name of a status code. */
+const char* gbx_status_string(gbx_status s);
+/* Library version, major * 10000 + minor * 100 + patch. */
+int32_t gbx_version(void);
+
+/* ------------------------------------------------------------------ graphs */
+
+typedef struct gbx_graph gbx_graph;
+
+/* Build flags for gbx_graph_build. */
+#define GBX_SYMMETRIZE 0x1u      /* store every edge in both directions (undirected graph) */
+#define GBX_DROP_SELF_LOOPS 0x2u /* drop edges u -> u */
+#define GBX_DEVICE_EDGES 0x4u    /* src and dst are device pointers (else host) */
+
+/*
+ * Build a graph from m directed edges src[e] -> dst[e] on vertices [0, n).
+ * Section 7.1: datasets are made undirected with self-loops and duplicate
+ * edges removed; duplicates are always removed here, the other two steps are
+ * selected by `flags`.  The library stores the adjacency matrix A (A(u,v) = 1
+ * for an edge u -> v) twice, as CSR of A (out-edges, the columns push reads)
+ * and CSR of A^T (in-edges, the rows pull reads, Algorithm 2 takes A^T); for
+ * a symmetrised graph the two are one array.  Neighbour lists are sorted
+ * ascending.  The build runs on the device (radix sort of packed (row, col)
+ * keys); it synchronises `stream` before returning.
+ * Errors: NULL_POINTER (out, or src/dst with m > 0), INVALID_VALUE (n < 1 or
+ * m < 0 or unknown flag bits), INVALID_INDEX (an endpoint outside [0, n)),
+ * OVERFLOW (2^31 or more stored edges), OUT_OF_MEMORY, CUDA.
+ * On success *out receives a handle to be released with gbx_graph_free.
+ */
+gbx_status gbx_graph_build(gbx_graph** out, int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                           uint32_t flags, void* stream);
+
+/* Release a graph and all device memory it owns.  NULL is accepted. */
+gbx_status gbx_graph_free(gbx_graph* g);
+
+/* Vertex count, stored-edge count (nnz of A) and whether A is symmetric. Any
+ * output pointer may be NULL. */
+gbx_status gbx_graph_info(const gbx_graph* g, int32_t* n, int64_t* nnz, int32_t* symmetric);
+
+/* Device pointers to the CSR arrays of A (transpose = 0) or A^T (transpose =
+ * 1): row_ptr int32[n + 1] and col int32[nnz].  Owned by the graph; valid
+ * until gbx_graph_free. */
+gbx_status gbx_graph_csr(const gbx_graph* g, int32_t transpose, const int32_t** row_ptr, const int32_t** col);
+
+/* Copy the CSR arrays of A (transpose = 0) or A^T (transpose = 1) into
+ * caller buffers row_ptr_dst (int32[n + 1]) and col_dst (int32[nnz]), each
+ * host or device memory.  Synchronous. */
+gbx_status gbx_graph_copy_csr(const gbx_graph* g, int32_t transpose, int32_t* row_ptr_dst, int32_t* col_dst);
+
+/* Wait for the work enqueued on `stream` and report device-side errors that
+ * kernels of this graph recorded since the last check (e.g. GBX_ERR_TIMEOUT
+ * from a bounded wait).  Clears the recorded error. */
+gbx_status gbx_graph_sync(gbx_graph* g, void* stream);
+
+/* ------------------------------------------------------------------ vectors */
+
+/* Vector formats (Section 6.3 stores the frontier as a DenseVector for
+ * row-based and a SparseVector for column-based matvec). */
+#define GBX_DENSE 0  /* data: uint8_t[size], entry i is true iff data[i] != 0 */
+#define GBX_SPARSE 1 /* data: int32_t[capacity] indices, ascending and unique (Section 3);
+                        *nnz (a device int32) holds how many are stored */
+
+/* A non-owning view of a vector in device memory. */
+typedef struct {
+    int32_t format;   /* GBX_DENSE or GBX_SPARSE */
+    int32_t size;     /* logical length; must equal the graph's n */
+    void* data;       /* device pointer, layout per format */
+    int32_t* nnz;     /* GBX_SPARSE: device pointer to the stored count (read for inputs,
+                         written for outputs); ignored for GBX_DENSE */
+    int32_t capacity; /* GBX_SPARSE: entries `data` can hold; an output needs capacity >= size */
+} gbx_vector;
+
+/* ------------------------------------------------------------------ descriptor */
+
+#define GBX_DIR_AUTO 0 /* push or pull chosen on the device (Section 6.3) */
+#define GBX_DIR_PUSH 1 /* column-based matvec (Eq 3/5, Algorithm 3) */
+#define GBX_DIR_PULL 2 /* row-based matvec (Eq 2/4, Algorithm 2) */
+
+#define GBX_HEUR_RATIO 0  /* Section 6.3: r = nnz(f)/M against alpha (up) and beta (down) */
+#define GBX_HEUR_BEAMER 1 /* Beamer's test that Section 6.3 starts from: nnz(m_f)/nnz(m_u) > alpha up */
+
+/*
+ * Operation modifiers.  Section 6.3 carries the sparse/dense switch point
+ * as a float in the descriptor; Section 3.2 adds the structural complement;
+ * Algorithm 2 adds accumulation and the optional early-exit break; Sections
+ * 5.2-5.4 are the BFS-level switches.  Initialise with gbx_desc_init and
+ * change fields.
+ */
+typedef struct {
+    int32_t transpose;       /* mxv: 1 computes A^T u (what BFS multiplies by), 0 computes A u */
+    int32_t mask_complement; /* use !mask instead of mask (Section 3.2) */
+    int32_t early_exit;      /* pull: stop a row at its first hit (Section 5.3; OR semiring only) */
+    int32_t accum;           /* w(i) = w_old(i) OR t(i) on passing rows, w_old(i) elsewhere */
+    int32_t direction;       /* GBX_DIR_AUTO / PUSH / PULL */
+    int32_t heuristic;       /* GBX_HEUR_RATIO or GBX_HEUR_BEAMER (BFS, AUTO only) */
+    float alpha;             /* push -> pull threshold (default 0.01) */
+    float beta;              /* pull -> push threshold (default 0.01) */
+    int32_t masking;         /* BFS pull visits only unvisited rows (Section 5.2; default 1) */
+    int32_t operand_reuse;   /* BFS pull tests "visited" instead of "in frontier" (Section 5.4; default 1) */
+    int32_t trace;           /* BFS: record per-level statistics (see gbx_bfs_trace) */
+    int32_t reserved[5];     /* must be 0 */
+} gbx_desc;
+
+/* Defaults: transpose 1, mask_complement 0, early_exit 1, accum 0,
+ * direction AUTO, heuristic RATIO, alpha = beta = 0.01 (Section 6.3),
+ * masking 1, operand_reuse 1, trace 0. */
+void gbx_desc_init(gbx_desc* d);
+
+/* ------------------------------------------------------------------ matvec */
+
+#define GBX_LOR_LAND 0 /* Boolean semiring ({0,1}, OR, AND, 0) of Algorithm 1 */
+
+/*
+ * w = (A u) .* mask  (or A^T u with desc->transpose), over `semiring`.
+ * Definition (Eq 2-5): t(i) = OR_j A'(i,j) AND u(j); pass(i) = (mask(i) != 0,
+ * 1 if mask is NULL) XOR desc->mask_complement; w(i) = pass(i) ? (accum ?
+ * w_old(i) OR t(i) : t(i)) : (accum ? w_old(i) : 0).  The result does not
+ * depend on the direction or on early exit (Section 4).
+ * Direction: PUSH expands the columns selected by u's nonzeros and dedups
+ * them with a bitmap (Eq 5); PULL computes only passing rows, each stopping at
+ * its first hit when early_exit is set (Eq 4, Algorithm 2); AUTO picks push
+ * when nnz(u)/n <= desc->alpha, else pull, on the device without a host round
+ * trip.  u, mask and w may be DENSE or SPARSE; a SPARSE w receives sorted
+ * indices and its count in *w->nnz.  All vectors live in device memory and
+ * must have size == n.  w must not alias u or mask.  Asynchronous on `stream`.
+ * Errors: NULL_POINTER, NOT_SUPPORTED (semiring), DIMENSION_MISMATCH,
+ * INVALID_VALUE (format, capacity < size for a SPARSE output, desc fields).
+ */
+gbx_status gbx_mxv(gbx_vector* w, const gbx_vector* mask, int32_t semiring, const gbx_graph* A,
+                   const gbx_vector* u, const gbx_desc* desc, void* stream);
+
+/* Work counters of the last gbx_mxv on A that ran with desc->trace = 1 (Table 1's
+ * cost terms): rows the pull computed, entries it examined (up to each row's
+ * first hit with early exit), nonzeros of u the push expanded, and the edges
+ * it expanded (nnz(m_f^+)).  Synchronises the stream of that call.  Any
+ * output pointer may be NULL. */
+gbx_status gbx_mxv_stats(const gbx_graph* A, int64_t* rows, int64_t* examined, int64_t* u_nnz, int64_t* edges);
+
+/* ------------------------------------------------------------------ BFS */
+
+/*
+ * Breadth-first search from `source` (Algorithm 1): every level runs the
+ * masked matvec f <- A^T f .* !v in the direction the descriptor selects
+ * (AUTO: start in push, switch per desc->heuristic after every level, decided
+ * on the device).  The whole level loop runs in one persistent cooperative
+ * kernel, so no level costs a host round trip.
+ * Outputs (device, int32[n], caller-owned): depth[v] = hops from the source
+ * (depth[source] = 0, unreached = -1); parent (may be NULL): parent[source] =
+ * source, parent[v] = some in-neighbour u of v with depth[u] = depth[v] - 1,
+ * unreached = -1.  Asynchronous on `stream`; device-side errors (bounded
+ * waits that ran out) are reported by gbx_graph_sync.
+ * Errors: NULL_POINTER, INVALID_INDEX (source), INVALID_VALUE (desc), CUDA.
+ */
+gbx_status gbx_bfs(gbx_graph* g, int32_t source, int32_t* depth, int32_t* parent, const gbx_desc* desc,
+                   void* stream);
+
+/*
+ * As gbx_bfs for `count` sources, writing into HOST buffers depth_host and
+ * parent_host (int32[count][n] each; parent_host may be NULL; pinned memory
+ * gives the fastest copies).  Results are computed on the device and copied
+ * back while the next source runs (two device buffer sets, a copy stream).
+ * Synchronous: returns when every result is in host memory.
+ */
+gbx_status gbx_bfs_host(gbx_graph* g, const int32_t* sources, int32_t count, int32_t* depth_host,
+                        int32_t* parent_host, const gbx_desc* desc, void* stream);
+
+/* Per-level statistics of the last gbx_bfs run with desc->trace = 1. */
+typedef struct {
+    int32_t direction; /* GBX_DIR_PUSH or GBX_DIR_PULL used for this level */
+    int32_t level;     /* L: the level that turns frontier F_L into F_{L+1} */
+    int64_t nf;        /* |F_L| */
+    int64_t mf;        /* out-edges of F_L, nnz(m_f^+) */
+    int64_t nu;        /* vertices not visited before this level */
+    int64_t nu_nz;     /* ... of which with nonzero in-degree */
+    int64_t mu;        /* in-edges of the unvisited vertices, nnz(m_u^-) (Eq 1) */
+    int64_t e_exam;    /* pull levels: in-edges examined, in ascending order, up to each row's
+                          first hit (all of them without early exit); -1 on push levels */
+    int64_t n_new;     /* |F_{L+1}| */
+    int64_t mf_new;    /* out-edges of F_{L+1} */
+} gbx_level;
+
+/* Copy the trace of the last traced BFS on g into levels[0..cap) and its
+ * length into *nlevels.  Synchronises the graph's last BFS stream. */
+gbx_status gbx_bfs_trace(gbx_graph* g, gbx_level* levels, int32_t cap, int32_t* nlevels);
+
+/* Upper bound, in nanoseconds, of every device-side wait in this library (the
+ * persistent kernels' grid barriers).  When it runs out the kernel records
+ * GBX_ERR_TIMEOUT and returns.  Default 5e9.  Process-wide. */
+gbx_status gbx_set_wait_timeout_ns(uint64_t ns);
+
+/* Failure-detection self-test: runs the persistent kernels' bounded grid
+ * barrier on g's own barrier and status words with one participant that never
+ * arrives, so every waiting block runs out of its timeout_ns limit, records
+ * GBX_ERR_TIMEOUT and returns.  Until gbx_graph_sync reports (and clears) that
+ * error, BFS kernels on g see it at their first barrier and return at once.
+ * Asynchronous on `stream`.  Causes no GPU fault. */
+gbx_status gbx_selftest_barrier_timeout(gbx_graph* g, uint64_t timeout_ns, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBX_H */

@@ -1,0 +1,239 @@
+// Internal declarations shared by the libgbx translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/gbx.h"
+
+namespace gbx {
+
+// ---------------------------------------------------------------- errors
+
+void set_error(const std::string& msg);
+void clear_error();
+uint64_t wait_timeout_ns();
+
+#define GBX_CUDA_TRY(expr)                                                                                \
+    do {                                                                                                  \
+        cudaError_t err__ = (expr);                                                                       \
+        if (err__ != cudaSuccess) {                                                                       \
+            ::gbx::set_error(std::string(#expr) + ": " + cudaGetErrorString(err__) + " (" + __FILE__ + ":" + \
+                             std::to_string(__LINE__) + ")");                                             \
+            return err__ == cudaErrorMemoryAllocation ? GBX_ERR_OUT_OF_MEMORY : GBX_ERR_CUDA;             \
+        }                                                                                                 \
+    } while (0)
+
+#define GBX_CHECK(cond, status, msg)       \
+    do {                                   \
+        if (!(cond)) {                     \
+            ::gbx::set_error(msg);         \
+            return (status);               \
+        }                                  \
+    } while (0)
+
+#define GBX_TRY(expr)                      \
+    do {                                   \
+        gbx_status st__ = (expr);          \
+        if (st__ != GBX_OK) return st__;   \
+    } while (0)
+
+// ---------------------------------------------------------------- device status words
+
+// Device-side status: [0] error code recorded by kernels (GBX_ERR_TIMEOUT ...),
+// [1] levels of the last BFS, [2] index of the first bad vertex (graph build).
+enum { ST_ERROR = 0, ST_LEVELS = 1, ST_BADINDEX = 2, ST_WORDS = 8 };
+
+// ---------------------------------------------------------------- level counters
+
+// One BFS level's counters, written with atomics by the level's producers.
+struct LevelCtr {
+    unsigned long long q;          // low 32 bits: queue entries, high 32: their out-degree sum
+    unsigned long long n_new;      // vertices discovered (all)
+    unsigned long long mf_new;     // out-degree sum of the discovered vertices
+    unsigned long long indeg_new;  // in-degree sum of the discovered vertices
+    unsigned long long e_exam;     // pull: in-edges examined
+    unsigned long long pad[3];
+};
+
+struct GridBar {
+    unsigned int count;
+    unsigned int gen;
+    unsigned int pad[30];
+};
+
+// Device-side trace record (mirrors gbx_level; nu / nu_nz filled on the host).
+struct LevelRec {
+    int32_t direction;
+    int32_t level;
+    long long nf, mf, mu, e_exam, n_new, mf_new;
+};
+
+constexpr int kTraceCap = 1 << 16;
+
+// ---------------------------------------------------------------- graph
+
+struct Graph {
+    int32_t n = 0;
+    int32_t nwords = 0;  // ceil(n / 32)
+    int64_t nnz = 0;
+    int32_t symmetric = 0;
+    int device = 0;
+    int num_sms = 0;
+    // CSR of A (out-edges) and of A^T (in-edges); in_* alias out_* when symmetric.
+    int32_t* out_ptr = nullptr;
+    int32_t* out_col = nullptr;
+    int32_t* in_ptr = nullptr;
+    int32_t* in_col = nullptr;
+    uint32_t* nz_in = nullptr;   // bit v set iff in-degree(v) > 0
+    uint32_t* nz_out = nullptr;  // bit v set iff out-degree(v) > 0
+    // scratch shared by the operations of this graph (ordered on one stream)
+    uint32_t* bm[4] = {nullptr, nullptr, nullptr, nullptr};  // n-bit bitmaps
+    int32_t* q[2] = {nullptr, nullptr};                       // frontier queues
+    int32_t* qp[2] = {nullptr, nullptr};                      // out-degree prefix per entry
+    int32_t* qd[2] = {nullptr, nullptr};                      // row start minus prefix per entry
+    int32_t* list = nullptr;                                  // n ints (mxv lists)
+    int32_t* scan_tmp = nullptr;                              // block sums for scans
+    LevelCtr* ctr = nullptr;                                  // 4 entries
+    GridBar* bar = nullptr;
+    LevelRec* trace = nullptr;                                // kTraceCap records
+    int32_t* status = nullptr;                                // ST_WORDS ints
+    int32_t* flag = nullptr;                                  // small device scratch (mxv decisions)
+    // host-side copies for gbx_bfs_host (allocated on first use)
+    int32_t* hdepth[2] = {nullptr, nullptr};
+    int32_t* hparent[2] = {nullptr, nullptr};
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_done[2] = {nullptr, nullptr};
+    cudaEvent_t ev_copied[2] = {nullptr, nullptr};
+    // BFS launch geometry
+    int bfs_blocks = 0;
+    cudaStream_t last_stream = nullptr;
+    int last_traced = 0;
+};
+
+// ---------------------------------------------------------------- primitives (prims.cu)
+
+constexpr int kScanBlock = 1024;      // threads per scan block
+constexpr int kScanItems = 4;         // items per thread
+constexpr int kScanTile = kScanBlock * kScanItems;
+
+// Exclusive scan of in[0 .. *count_dev) (or [0, count_max) when count_dev is NULL) into
+// out[0 .. count], with out[count] = total.  tmp needs scan_tmp_ints(count_max) ints.
+size_t scan_tmp_ints(int64_t count_max);
+gbx_status exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t count_max, const int32_t* count_dev,
+                              int32_t* tmp, cudaStream_t s);
+
+// Stable LSD radix sort of 64-bit keys on the low `bits` bits; result in *keys (buffers swapped as needed).
+gbx_status radix_sort_u64(unsigned long long** keys, unsigned long long** alt, int64_t n, int bits, cudaStream_t s);
+
+// Bitmap helpers.
+gbx_status pack_dense_to_bitmap(const uint8_t* dense, int32_t n, uint32_t invert, uint32_t* bm, cudaStream_t s);
+// Entries outside [0, n) are ignored.
+gbx_status scatter_list_to_bitmap(const int32_t* list, const int32_t* count_dev, int32_t cap, int32_t n, uint32_t* bm,
+                                  cudaStream_t s);
+gbx_status fill_bitmap(uint32_t* bm, int32_t n, uint32_t value, cudaStream_t s);
+gbx_status invert_bitmap(uint32_t* bm, int32_t n, cudaStream_t s);
+gbx_status bitmap_to_list(const uint32_t* bm, int32_t n, int32_t* list, int32_t* count_dev, int32_t* scan_out,
+                          int32_t* tmp, cudaStream_t s);
+gbx_status bitmap_to_dense(const uint32_t* bm, int32_t n, const uint8_t* old_dense, uint8_t* out, cudaStream_t s);
+
+// ---------------------------------------------------------------- device helpers
+
+__device__ __forceinline__ unsigned long long global_timer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_volatile_i32(const int32_t* p) { return *(const volatile int32_t*)p; }
+
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
+    return *(const volatile unsigned long long*)p;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ bool bit_test(const uint32_t* bm, int32_t v) { return (bm[v >> 5] >> (v & 31)) & 1u; }
+
+// Inclusive warp scan (sum) of a 32-bit value.
+__device__ __forceinline__ uint32_t warp_inclusive_sum(uint32_t x) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// Grid-wide barrier for persistent cooperative kernels.  Bounded: a block that
+// waits longer than timeout_ns records GBX_ERR_TIMEOUT in status[ST_ERROR] and
+// every block returns false once any block has recorded an error.
+__device__ __forceinline__ bool grid_barrier(GridBar* bar, unsigned int nblocks, int32_t* status,
+                                             unsigned long long timeout_ns) {
+    __shared__ int ok_shared;
+    __syncthreads();
+    if (threadIdx.x == 0 && ld_volatile_i32(status + ST_ERROR) != 0) {
+        ok_shared = 0;  // an error is pending: do not arrive, just leave
+    } else if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned int gen = ld_acquire_u32(&bar->gen);
+        __threadfence();
+        const unsigned int arrived = atomicAdd(&bar->count, 1u);
+        if (arrived == nblocks - 1) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            atomicAdd(&bar->gen, 1u);
+        } else {
+            const unsigned long long t0 = global_timer_ns();
+            while (ld_acquire_u32(&bar->gen) == gen) {
+                if (ld_volatile_i32(status + ST_ERROR) != 0) {
+                    ok = 0;
+                    break;
+                }
+                if (global_timer_ns() - t0 > timeout_ns) {
+                    atomicCAS(status + ST_ERROR, 0, (int)GBX_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        if (ok && ld_volatile_i32(status + ST_ERROR) != 0) ok = 0;
+        __threadfence();
+        ok_shared = ok;
+    }
+    __syncthreads();
+    return ok_shared != 0;
+}
+
+inline unsigned int div_up(int64_t a, int64_t b) { return (unsigned int)((a + b - 1) / b); }
+
+inline gbx_status check_graph(const gbx_graph* g) {
+    GBX_CHECK(g != nullptr, GBX_ERR_NULL_POINTER, "graph handle is NULL");
+    return GBX_OK;
+}
+
+inline Graph* as_impl(gbx_graph* g) { return reinterpret_cast<Graph*>(g); }
+inline const Graph* as_impl(const gbx_graph* g) { return reinterpret_cast<const Graph*>(g); }
+
+gbx_status graph_scratch_alloc(Graph* g);
+
+}  // namespace gbx

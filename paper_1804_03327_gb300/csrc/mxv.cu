@@ -1,0 +1,334 @@
+// GrB_mxv over the Boolean semiring: the four matvec variants of Table 1.
+//
+//   row-based (pull, Eq 2 / Eq 4, Algorithm 2): one warp per 32 output rows;
+//     only rows whose mask test passes are computed; each row ORs u over its
+//     entries, stopping at the first hit when early exit is on (Section 5.3).
+//   column-based (push, Eq 3 / Eq 5): the columns selected by u's nonzeros
+//     are expanded with their edges split evenly over warps (exclusive prefix
+//     of the selected columns' lengths); every hit that passes the mask sets
+//     its bit in a result bitmap with atomicOr, which merges the columns
+//     exactly (the multiway merge of Section 3.1, done by a bitmap instead of
+//     the radix sort of Algorithm 3).
+// The result bitmap is then written out as a dense byte vector or as a sorted
+// index list (Section 3: sparse vectors are sorted lists).
+#include "gbx_internal.cuh"
+
+namespace gbx {
+
+constexpr int kMxvThreads = 256;
+constexpr int kMxvProbe = 16;
+
+// Per-call counters (desc.trace): [0] rows computed by pull, [1] entries
+// examined by pull, [2] nonzeros of u expanded by push, [3] edges expanded.
+struct MxvStats {
+    unsigned long long rows, exam, ucount, edges, pad[4];
+};
+
+__device__ __forceinline__ bool dir_enabled(const int32_t* flag, int want) { return !flag || *flag == want; }
+
+__global__ void __launch_bounds__(kMxvThreads) mxv_pull_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                                                                const uint32_t* __restrict__ nzrows,
+                                                                const uint32_t* __restrict__ ubm,
+                                                                const uint32_t* __restrict__ pass, uint32_t* __restrict__ R,
+                                                                int32_t nwords, int early_exit, const int32_t* flag,
+                                                                MxvStats* stats) {
+    if (!dir_enabled(flag, GBX_DIR_PULL)) return;
+    const int lane = threadIdx.x & 31;
+    const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+    unsigned long long rows = 0, exam = 0;
+    for (int32_t w = gwarp; w < nwords; w += nwarps) {
+        const uint32_t cand = (pass ? pass[w] : 0xffffffffu) & nzrows[w];
+        if (cand == 0) {
+            if (lane == 0) R[w] = 0u;
+            continue;
+        }
+        const int32_t i = (w << 5) + lane;
+        const bool mine = (cand >> lane) & 1u;
+        int32_t k = 0, end = 0;
+        bool found = false, done = false;
+        if (mine) {
+            rows += 1;
+            k = ptr[i];
+            end = ptr[i + 1];
+            const int32_t lim = end < k + kMxvProbe ? end : k + kMxvProbe;
+            while (k < lim) {
+                const bool h = bit_test(ubm, col[k]);
+                exam += 1;
+                ++k;
+                if (h) {
+                    found = true;
+                    if (early_exit) {
+                        done = true;
+                        break;
+                    }
+                }
+            }
+        }
+        uint32_t pend = __ballot_sync(0xffffffffu, mine && !done && k < end);
+        while (pend) {
+            const int t = __ffs(pend) - 1;
+            pend &= pend - 1;
+            int32_t kk = __shfl_sync(0xffffffffu, k, t);
+            const int32_t ee = __shfl_sync(0xffffffffu, end, t);
+            bool tf = __shfl_sync(0xffffffffu, found, t);
+            unsigned long long tx = 0;
+            for (; kk < ee; kk += 32) {
+                const int32_t idx = kk + lane;
+                const uint32_t hb = __ballot_sync(0xffffffffu, idx < ee && bit_test(ubm, col[idx]));
+                if (hb) {
+                    tf = true;
+                    if (early_exit) {
+                        tx += (unsigned long long)(__ffs(hb));
+                        break;
+                    }
+                }
+                tx += (unsigned long long)(ee - kk < 32 ? ee - kk : 32);
+            }
+            if (lane == t) {
+                found = tf;
+                exam += tx;
+            }
+        }
+        const uint32_t fm = __ballot_sync(0xffffffffu, found);
+        if (lane == 0) R[w] = fm;
+    }
+    if (stats) {
+        rows = warp_sum_u64(rows);
+        exam = warp_sum_u64(exam);
+        if (lane == 0) {
+            if (rows) atomicAdd(&stats->rows, rows);
+            if (exam) atomicAdd(&stats->exam, exam);
+        }
+    }
+}
+
+__global__ void mxv_degrees_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ list,
+                                   const int32_t* count_dev, int32_t cap, int32_t n, int32_t* __restrict__ deg,
+                                   const int32_t* flag) {
+    if (!dir_enabled(flag, GBX_DIR_PUSH)) return;
+    // same count as the scan that follows (clamped to n); entries past the
+    // capacity or outside [0, n) expand nothing
+    const int32_t count = min(*count_dev, n);
+    for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x) {
+        const int32_t u = k < cap ? list[k] : -1;
+        deg[k] = (u >= 0 && u < n) ? ptr[u + 1] - ptr[u] : 0;
+    }
+}
+
+// Number of entries of the warp-held sorted window (one value per lane) that are <= e.
+__device__ __forceinline__ int window_rank(long long win, long long e) {
+    int c = 0;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) c += (__shfl_sync(0xffffffffu, win, j) <= e) ? 1 : 0;
+    return c;
+}
+
+__device__ __forceinline__ int32_t last_le(const int32_t* pre, int32_t lo, int32_t hi, long long e) {
+    while (lo < hi) {
+        const int32_t mid = lo + ((hi - lo + 1) >> 1);
+        if ((long long)pre[mid] <= e)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kMxvThreads) mxv_push_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                                                                const int32_t* __restrict__ list, const int32_t* count_dev,
+                                                                int32_t cap, const int32_t* __restrict__ pre,
+                                                                const uint32_t* __restrict__ pass, uint32_t* R,
+                                                                const int32_t* flag, MxvStats* stats) {
+    if (!dir_enabled(flag, GBX_DIR_PUSH)) return;
+    const int lane = threadIdx.x & 31;
+    const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+    const int32_t count = min(*count_dev, cap);  // cap = n here: matches the scan's count
+    if (count <= 0) return;
+    const long long E = pre[count];
+    if (stats && gwarp == 0 && lane == 0) {
+        atomicAdd(&stats->ucount, (unsigned long long)count);
+        atomicAdd(&stats->edges, (unsigned long long)E);
+    }
+    long long chunk = (E + nwarps - 1) / nwarps;
+    chunk = chunk < 64 ? 64 : ((chunk + 31) & ~31ll);
+    for (long long e0 = (long long)gwarp * chunk; e0 < E; e0 += (long long)nwarps * chunk) {
+        const long long e1 = e0 + chunk < E ? e0 + chunk : E;
+        int32_t k = 0;
+        if (lane == 0) k = last_le(pre, 0, count - 1, e0);
+        k = __shfl_sync(0xffffffffu, k, 0);
+        for (long long base = e0; base < e1; base += 32) {
+            const int32_t wi = k + 1 + lane;
+            const long long win = wi < count ? (long long)pre[wi] : (long long)INT64_MAX;
+            const long long e = base + lane;
+            const int c = window_rank(win, e);
+            int32_t kk = k + c;
+            if (c == 32) kk = last_le(pre, k + 32, count - 1, e);  // many empty columns in a row
+            if (e < e1) {
+                const int32_t u = list[kk];
+                const int32_t v = col[ptr[u] + (int32_t)(e - pre[kk])];
+                if (!pass || bit_test(pass, v)) {
+                    const uint32_t bit = 1u << (v & 31);
+                    if (!(__ldcg(R + (v >> 5)) & bit)) atomicOr(R + (v >> 5), bit);
+                }
+            }
+            k = __shfl_sync(0xffffffffu, kk, 31);
+        }
+    }
+}
+
+// AUTO: push when nnz(u)/n <= alpha (input sparsity), else pull (Section 6.3).
+__global__ void mxv_decide_kernel(const int32_t* count_dev, int32_t n, float alpha, int32_t* flag) {
+    const double r = (double)(*count_dev) / (double)n;
+    *flag = r <= (double)alpha ? GBX_DIR_PUSH : GBX_DIR_PULL;
+}
+
+__global__ void zero_stats_kernel(MxvStats* s) {
+    MxvStats z = {};
+    *s = z;
+}
+
+static gbx_status check_vec(const gbx_vector* v, int32_t n, const char* name, bool output) {
+    GBX_CHECK(v->format == GBX_DENSE || v->format == GBX_SPARSE, GBX_ERR_INVALID_VALUE,
+              std::string(name) + ": unknown format");
+    GBX_CHECK(v->size == n, GBX_ERR_DIMENSION_MISMATCH, std::string(name) + ": size differs from the graph's n");
+    GBX_CHECK(v->data != nullptr, GBX_ERR_NULL_POINTER, std::string(name) + ": data is NULL");
+    if (v->format == GBX_SPARSE) {
+        GBX_CHECK(v->nnz != nullptr, GBX_ERR_NULL_POINTER, std::string(name) + ": nnz is NULL");
+        GBX_CHECK(v->capacity >= 0, GBX_ERR_INVALID_VALUE, std::string(name) + ": capacity < 0");
+        if (output)
+            GBX_CHECK(v->capacity >= v->size, GBX_ERR_INVALID_VALUE,
+                      std::string(name) + ": a sparse output needs capacity >= size");
+    }
+    return GBX_OK;
+}
+
+}  // namespace gbx
+
+using namespace gbx;
+
+extern "C" gbx_status gbx_mxv(gbx_vector* w, const gbx_vector* mask, int32_t semiring, const gbx_graph* A,
+                              const gbx_vector* u, const gbx_desc* desc, void* stream) {
+    clear_error();
+    GBX_TRY(check_graph(A));
+    GBX_CHECK(w != nullptr && u != nullptr, GBX_ERR_NULL_POINTER, "w or u is NULL");
+    GBX_CHECK(semiring == GBX_LOR_LAND, GBX_ERR_NOT_SUPPORTED, "only the Boolean semiring GBX_LOR_LAND is supported");
+    Graph* G = const_cast<Graph*>(as_impl(A));
+    const int32_t n = G->n;
+    GBX_TRY(check_vec(u, n, "u", false));
+    GBX_TRY(check_vec(w, n, "w", true));
+    if (mask) GBX_TRY(check_vec(mask, n, "mask", false));
+    GBX_CHECK(w->data != u->data && (!mask || w->data != mask->data), GBX_ERR_INVALID_VALUE,
+              "w must not alias u or mask");
+    gbx_desc d;
+    if (desc)
+        d = *desc;
+    else
+        gbx_desc_init(&d);
+    GBX_CHECK(d.direction >= GBX_DIR_AUTO && d.direction <= GBX_DIR_PULL, GBX_ERR_INVALID_VALUE, "desc.direction");
+    GBX_CHECK(d.alpha >= 0.0f && d.alpha == d.alpha, GBX_ERR_INVALID_VALUE, "desc.alpha must be >= 0");
+    for (int k = 0; k < 5; ++k) GBX_CHECK(d.reserved[k] == 0, GBX_ERR_INVALID_VALUE, "desc.reserved must be 0");
+    cudaStream_t s = (cudaStream_t)stream;
+
+    // w = A' u with A' = A^T (transpose) or A.  Pull reads rows of A' (CSR of A'),
+    // push reads the columns of A' selected by u, i.e. rows of (A')^T.
+    const int32_t* pull_ptr = d.transpose ? G->in_ptr : G->out_ptr;
+    const int32_t* pull_col = d.transpose ? G->in_col : G->out_col;
+    const uint32_t* pull_nz = d.transpose ? G->nz_in : G->nz_out;
+    const int32_t* push_ptr = d.transpose ? G->out_ptr : G->in_ptr;
+    const int32_t* push_col = d.transpose ? G->out_col : G->in_col;
+
+    uint32_t* ubm = G->bm[0];
+    uint32_t* pass = G->bm[1];
+    uint32_t* R = G->bm[2];
+    int32_t* list_count = G->flag + 0;
+    int32_t* dflag = G->flag + 1;
+    MxvStats* stats = d.trace ? reinterpret_cast<MxvStats*>(G->ctr + 3) : nullptr;
+    if (stats) zero_stats_kernel<<<1, 1, 0, s>>>(stats);
+
+    const int dir = d.direction;
+    const bool want_pull = dir != GBX_DIR_PUSH;
+    const bool want_push = dir != GBX_DIR_PULL;
+
+    // u as a bitmap (pull) and as a sorted list (push)
+    const int32_t* ulist = nullptr;
+    const int32_t* ucount = nullptr;
+    int32_t ucap = n;
+    if (u->format == GBX_DENSE) {
+        GBX_TRY(pack_dense_to_bitmap((const uint8_t*)u->data, n, 0, ubm, s));
+        if (want_push) {
+            GBX_TRY(bitmap_to_list(ubm, n, G->list, list_count, G->qd[0], G->scan_tmp, s));
+            ulist = G->list;
+            ucount = list_count;
+        }
+    } else {
+        ulist = (const int32_t*)u->data;
+        ucount = u->nnz;
+        ucap = u->capacity < n ? u->capacity : n;
+        if (want_pull) {
+            GBX_TRY(fill_bitmap(ubm, n, 0u, s));
+            GBX_TRY(scatter_list_to_bitmap(ulist, ucount, ucap, n, ubm, s));
+        }
+    }
+    // mask -> bitmap of passing rows; pass = m XOR complement (Algorithm 2, line 3)
+    const uint32_t* pass_bm = nullptr;
+    bool nothing_passes = false;
+    if (!mask) {
+        nothing_passes = d.mask_complement != 0;
+    } else if (mask->format == GBX_DENSE) {
+        GBX_TRY(pack_dense_to_bitmap((const uint8_t*)mask->data, n, d.mask_complement ? 1u : 0u, pass, s));
+        pass_bm = pass;
+    } else {
+        GBX_TRY(fill_bitmap(pass, n, 0u, s));
+        GBX_TRY(scatter_list_to_bitmap((const int32_t*)mask->data, mask->nnz, mask->capacity, n, pass, s));
+        if (d.mask_complement) GBX_TRY(invert_bitmap(pass, n, s));
+        pass_bm = pass;
+    }
+    GBX_TRY(fill_bitmap(R, n, 0u, s));
+    if (!nothing_passes) {
+        const int32_t* flag = nullptr;
+        if (dir == GBX_DIR_AUTO) {
+            mxv_decide_kernel<<<1, 1, 0, s>>>(ucount, n, d.alpha, dflag);
+            flag = dflag;
+        }
+        if (want_push) {
+            int32_t* deg = G->q[0];
+            int32_t* pre = G->qp[0];
+            mxv_degrees_kernel<<<max(1u, min(div_up(n, 256), 152u * 16)), 256, 0, s>>>(push_ptr, ulist, ucount, ucap,
+                                                                                    n, deg, flag);
+            GBX_TRY(exclusive_scan_i32(deg, pre, n, ucount, G->scan_tmp, s));
+            mxv_push_kernel<<<G->num_sms * 8, kMxvThreads, 0, s>>>(push_ptr, push_col,
+                                                                    ulist, ucount, n, pre, pass_bm, R, flag, stats);
+        }
+        if (want_pull) {
+            mxv_pull_kernel<<<G->num_sms * 8, kMxvThreads, 0, s>>>(pull_ptr, pull_col, pull_nz, ubm, pass_bm, R,
+                                                                    G->nwords, d.early_exit ? 1 : 0, flag, stats);
+        }
+    }
+    // output
+    if (w->format == GBX_DENSE) {
+        GBX_TRY(bitmap_to_dense(R, n, d.accum ? (const uint8_t*)w->data : nullptr, (uint8_t*)w->data, s));
+    } else {
+        if (d.accum) GBX_TRY(scatter_list_to_bitmap((const int32_t*)w->data, w->nnz, w->capacity, n, R, s));
+        GBX_TRY(bitmap_to_list(R, n, (int32_t*)w->data, w->nnz, G->qd[1], G->scan_tmp, s));
+    }
+    GBX_CUDA_TRY(cudaGetLastError());
+    G->last_stream = s;
+    return GBX_OK;
+}
+
+extern "C" gbx_status gbx_mxv_stats(const gbx_graph* A, int64_t* rows, int64_t* examined, int64_t* u_nnz,
+                                    int64_t* edges) {
+    clear_error();
+    GBX_TRY(check_graph(A));
+    const Graph* G = as_impl(A);
+    if (G->last_stream) GBX_CUDA_TRY(cudaStreamSynchronize(G->last_stream));
+    MxvStats st;
+    GBX_CUDA_TRY(cudaMemcpy(&st, G->ctr + 3, sizeof(st), cudaMemcpyDeviceToHost));
+    if (rows) *rows = (int64_t)st.rows;
+    if (examined) *examined = (int64_t)st.exam;
+    if (u_nnz) *u_nnz = (int64_t)st.ucount;
+    if (edges) *edges = (int64_t)st.edges;
+    return GBX_OK;
+}

@@ -1,0 +1,297 @@
+"""Thin Python binding of libgbx.so (the C ABI declared in include/gbx.h).
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels.  Functions keep the C names without the ``gbx_`` prefix.  Device
+buffers are CUDA tensors (PyTorch provides device memory and streams; it does
+no compute here).  Failing calls raise ``GbxError`` with the library's status
+and message.  If libgbx.so has not been built the import of a function raises
+instead of falling back to anything.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+OK = 0
+ERR_INVALID_VALUE = 1
+ERR_INVALID_INDEX = 2
+ERR_DIMENSION_MISMATCH = 3
+ERR_OUT_OF_MEMORY = 4
+ERR_NOT_SUPPORTED = 5
+ERR_TIMEOUT = 6
+ERR_CUDA = 7
+ERR_OVERFLOW = 8
+ERR_BUSY = 9
+ERR_NULL_POINTER = 10
+
+SYMMETRIZE = 0x1
+DROP_SELF_LOOPS = 0x2
+DEVICE_EDGES = 0x4
+DENSE = 0
+SPARSE = 1
+DIR_AUTO = 0
+DIR_PUSH = 1
+DIR_PULL = 2
+HEUR_RATIO = 0
+HEUR_BEAMER = 1
+LOR_LAND = 0
+
+EXPORTED = [
+    "gbx_last_error", "gbx_status_string", "gbx_version", "gbx_graph_build", "gbx_graph_free", "gbx_graph_info",
+    "gbx_graph_csr", "gbx_graph_copy_csr", "gbx_graph_sync", "gbx_desc_init", "gbx_mxv", "gbx_mxv_stats",
+    "gbx_bfs", "gbx_bfs_host", "gbx_bfs_trace", "gbx_set_wait_timeout_ns", "gbx_selftest_barrier_timeout",
+]
+
+
+class GbxError(RuntimeError):
+    def __init__(self, status: int, fn: str, message: str):
+        super().__init__(f"{fn}: status {status} ({message})")
+        self.status = status
+
+
+class Vector(ctypes.Structure):
+    _fields_ = [("format", ctypes.c_int32), ("size", ctypes.c_int32), ("data", ctypes.c_void_p),
+                ("nnz", ctypes.c_void_p), ("capacity", ctypes.c_int32)]
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [("transpose", ctypes.c_int32), ("mask_complement", ctypes.c_int32), ("early_exit", ctypes.c_int32),
+                ("accum", ctypes.c_int32), ("direction", ctypes.c_int32), ("heuristic", ctypes.c_int32),
+                ("alpha", ctypes.c_float), ("beta", ctypes.c_float), ("masking", ctypes.c_int32),
+                ("operand_reuse", ctypes.c_int32), ("trace", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+
+
+class Level(ctypes.Structure):
+    _fields_ = [("direction", ctypes.c_int32), ("level", ctypes.c_int32), ("nf", ctypes.c_int64),
+                ("mf", ctypes.c_int64), ("nu", ctypes.c_int64), ("nu_nz", ctypes.c_int64), ("mu", ctypes.c_int64),
+                ("e_exam", ctypes.c_int64), ("n_new", ctypes.c_int64), ("mf_new", ctypes.c_int64)]
+
+
+LEVEL_FIELDS = ["direction", "level", "nf", "mf", "nu", "nu_nz", "mu", "e_exam", "n_new", "mf_new"]
+
+
+def lib_path() -> str:
+    return _build.LIB_PATH
+
+
+def load():
+    """Load libgbx.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = lib_path()
+            if not os.path.exists(path):
+                raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                                   "or python -m paper_1804_03327_gb300.build")
+            L = ctypes.CDLL(path)
+            p, i32, i64, u32, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64
+            sigs = {
+                "gbx_last_error": (ctypes.c_char_p, []),
+                "gbx_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+                "gbx_version": (i32, []),
+                "gbx_graph_build": (ctypes.c_int, [ctypes.POINTER(p), i32, i64, p, p, u32, p]),
+                "gbx_graph_free": (ctypes.c_int, [p]),
+                "gbx_graph_info": (ctypes.c_int, [p, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i32)]),
+                "gbx_graph_csr": (ctypes.c_int, [p, i32, ctypes.POINTER(p), ctypes.POINTER(p)]),
+                "gbx_graph_copy_csr": (ctypes.c_int, [p, i32, p, p]),
+                "gbx_graph_sync": (ctypes.c_int, [p, p]),
+                "gbx_desc_init": (None, [ctypes.POINTER(Desc)]),
+                "gbx_mxv": (ctypes.c_int, [ctypes.POINTER(Vector), ctypes.POINTER(Vector), i32, p,
+                                           ctypes.POINTER(Vector), ctypes.POINTER(Desc), p]),
+                "gbx_mxv_stats": (ctypes.c_int, [p] + [ctypes.POINTER(i64)] * 4),
+                "gbx_bfs": (ctypes.c_int, [p, i32, p, p, ctypes.POINTER(Desc), p]),
+                "gbx_bfs_host": (ctypes.c_int, [p, p, i32, p, p, ctypes.POINTER(Desc), p]),
+                "gbx_bfs_trace": (ctypes.c_int, [p, ctypes.POINTER(Level), i32, ctypes.POINTER(i32)]),
+                "gbx_set_wait_timeout_ns": (ctypes.c_int, [u64]),
+                "gbx_selftest_barrier_timeout": (ctypes.c_int, [p, u64, p]),
+            }
+            for name, (res, args) in sigs.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(status: int, fn: str):
+    if status != OK:
+        msg = load().gbx_last_error().decode(errors="replace")
+        raise GbxError(status, fn, msg)
+
+
+def _stream_ptr(stream):
+    """cudaStream_t of a torch stream (None: the current torch stream)."""
+    if isinstance(stream, int):
+        return stream
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def status_string(status: int) -> str:
+    return load().gbx_status_string(status).decode()
+
+
+def version() -> int:
+    return int(load().gbx_version())
+
+
+def desc_init(**fields) -> Desc:
+    d = Desc()
+    load().gbx_desc_init(ctypes.byref(d))
+    for k, v in fields.items():
+        if not hasattr(d, k):
+            raise AttributeError(k)
+        setattr(d, k, v)
+    return d
+
+
+def selftest_barrier_timeout(g: "Graph", timeout_ns: int, stream=None):
+    _check(load().gbx_selftest_barrier_timeout(g.handle, int(timeout_ns), _stream_ptr(stream)),
+           "gbx_selftest_barrier_timeout")
+
+
+def set_wait_timeout_ns(ns: int):
+    _check(load().gbx_set_wait_timeout_ns(int(ns)), "gbx_set_wait_timeout_ns")
+
+
+class Graph:
+    """Owning handle of a gbx_graph."""
+
+    def __init__(self, handle):
+        self._h = handle
+
+    @property
+    def handle(self):
+        return self._h
+
+    def free(self):
+        if self._h:
+            _check(load().gbx_graph_free(self._h), "gbx_graph_free")
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def info(self):
+        n, nnz, sym = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32()
+        _check(load().gbx_graph_info(self._h, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(sym)),
+               "gbx_graph_info")
+        return n.value, nnz.value, bool(sym.value)
+
+
+def graph_build(n: int, src, dst, symmetrize: bool = True, drop_self_loops: bool = True, stream=None) -> Graph:
+    """Build from host numpy int32 arrays or CUDA int32 tensors (src[e] -> dst[e])."""
+    flags = (SYMMETRIZE if symmetrize else 0) | (DROP_SELF_LOOPS if drop_self_loops else 0)
+    if isinstance(src, np.ndarray):
+        src = np.ascontiguousarray(src, dtype=np.int32)
+        dst = np.ascontiguousarray(dst, dtype=np.int32)
+        sp, dp = src.ctypes.data, dst.ctypes.data
+        m = len(src)
+        sptr = None
+    else:
+        if src.dtype != dst.dtype or str(src.dtype) != "torch.int32" or not src.is_cuda:
+            raise TypeError("device edges must be CUDA int32 tensors")
+        src, dst = src.contiguous(), dst.contiguous()
+        sp, dp = src.data_ptr(), dst.data_ptr()
+        m = src.numel()
+        flags |= DEVICE_EDGES
+        sptr = _stream_ptr(stream)
+    h = ctypes.c_void_p()
+    st = load().gbx_graph_build(ctypes.byref(h), int(n), int(m), sp, dp, flags,
+                                sptr if sptr is not None else (_stream_ptr(stream) if _torch_cuda() else None))
+    _check(st, "gbx_graph_build")
+    return Graph(h.value)
+
+
+def _torch_cuda() -> bool:
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def graph_copy_csr(g: Graph, transpose: bool = False):
+    """(row_ptr, col) of A (or A^T) as host numpy int32 arrays."""
+    n, nnz, _ = g.info()
+    row_ptr = np.empty(n + 1, dtype=np.int32)
+    col = np.empty(max(nnz, 1), dtype=np.int32)
+    _check(load().gbx_graph_copy_csr(g.handle, int(transpose), row_ptr.ctypes.data, col.ctypes.data),
+           "gbx_graph_copy_csr")
+    return row_ptr, col[:nnz]
+
+
+def graph_sync(g: Graph, stream=None):
+    _check(load().gbx_graph_sync(g.handle, _stream_ptr(stream)), "gbx_graph_sync")
+
+
+def dense(t) -> Vector:
+    """View of a CUDA uint8 tensor as a GBX_DENSE vector."""
+    assert t.is_cuda and str(t.dtype) == "torch.uint8" and t.is_contiguous()
+    return Vector(DENSE, t.numel(), t.data_ptr(), None, 0)
+
+
+def sparse(indices, nnz, size: int) -> Vector:
+    """View of CUDA int32 tensors (indices[capacity], nnz[1]) as a GBX_SPARSE vector."""
+    assert indices.is_cuda and str(indices.dtype) == "torch.int32" and indices.is_contiguous()
+    assert nnz.is_cuda and str(nnz.dtype) == "torch.int32"
+    return Vector(SPARSE, int(size), indices.data_ptr(), nnz.data_ptr(), indices.numel())
+
+
+def mxv(w: Vector, mask, semiring: int, A: Graph, u: Vector, desc: Desc | None = None, stream=None):
+    st = load().gbx_mxv(ctypes.byref(w), ctypes.byref(mask) if mask is not None else None, int(semiring), A.handle,
+                        ctypes.byref(u), ctypes.byref(desc) if desc is not None else None, _stream_ptr(stream))
+    _check(st, "gbx_mxv")
+
+
+def mxv_stats(A: Graph):
+    vals = [ctypes.c_int64() for _ in range(4)]
+    _check(load().gbx_mxv_stats(A.handle, *[ctypes.byref(v) for v in vals]), "gbx_mxv_stats")
+    return dict(zip(["rows", "examined", "u_nnz", "edges"], [v.value for v in vals]))
+
+
+def bfs(g: Graph, source: int, depth, parent=None, desc: Desc | None = None, stream=None):
+    """BFS into CUDA int32 tensors depth[n] and (optionally) parent[n]."""
+    st = load().gbx_bfs(g.handle, int(source), depth.data_ptr(), parent.data_ptr() if parent is not None else None,
+                        ctypes.byref(desc) if desc is not None else None, _stream_ptr(stream))
+    _check(st, "gbx_bfs")
+
+
+def bfs_host(g: Graph, sources, depth_host: np.ndarray, parent_host: np.ndarray | None = None,
+             desc: Desc | None = None, stream=None):
+    """BFS for every source into host arrays depth_host[count, n] (and parent_host)."""
+    srcs = np.ascontiguousarray(sources, dtype=np.int32)
+    dptr = depth_host.data_ptr() if hasattr(depth_host, "data_ptr") else depth_host.ctypes.data
+    pptr = None
+    if parent_host is not None:
+        pptr = parent_host.data_ptr() if hasattr(parent_host, "data_ptr") else parent_host.ctypes.data
+    st = load().gbx_bfs_host(g.handle, srcs.ctypes.data, len(srcs), dptr, pptr,
+                             ctypes.byref(desc) if desc is not None else None, _stream_ptr(stream))
+    _check(st, "gbx_bfs_host")
+
+
+def bfs_trace(g: Graph, cap: int = 1 << 16) -> np.ndarray:
+    """Per-level records of the last traced BFS as a numpy structured array."""
+    buf = (Level * cap)()
+    nl = ctypes.c_int32()
+    _check(load().gbx_bfs_trace(g.handle, buf, cap, ctypes.byref(nl)), "gbx_bfs_trace")
+    k = min(nl.value, cap)
+    dt = np.dtype([(f, np.int64) for f in LEVEL_FIELDS])
+    out = np.zeros(k, dtype=dt)
+    for i in range(k):
+        for f in LEVEL_FIELDS:
+            out[i][f] = getattr(buf[i], f)
+    return out

@@ -1,0 +1,266 @@
+"""GPU parity: graph build and BFS through the C ABI against the CPU oracle.
+
+Depths must match bit-exactly; parents must be valid (early exit and atomic
+claims may pick any parent); per-level counts and the direction schedule
+must match the oracle's trace and its Section 6.3 rule exactly."""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from checks import assert_valid_parents
+from paper_1804_03327_gb300 import gbx
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    gbx.load()
+    yield
+    gbx.set_wait_timeout_ns(5_000_000_000)
+
+
+_cache = {}
+
+
+def graphs(name):
+    if name not in _cache:
+        if name == "rmat10":
+            n, s, d = synth.rmat_edges(10, 16, seed=1)
+            sym = True
+        elif name == "rmat14":
+            n, s, d = synth.rmat_edges(14, 16, seed=3)
+            sym = True
+        elif name == "rmat12-directed":
+            n, s, d = synth.rmat_edges(12, 8, seed=4)
+            sym = False
+        elif name == "grid64":
+            n, s, d = synth.grid_edges(64, 64, p_delete=0.01, seed=1)
+            sym = True
+        elif name == "grid-exact":
+            n, s, d = synth.grid_edges(40, 25, p_delete=0.0)
+            sym = True
+        elif name == "er-directed":
+            n, s, d = synth.er_edges(300, 0.01, seed=7, directed=True)
+            sym = False
+        else:
+            raise KeyError(name)
+        _cache[name] = (n, s, d, sym, oracle.graph(n, s, d, symmetrize=sym), gbx.graph_build(n, s, d, symmetrize=sym))
+    return _cache[name]
+
+
+def run_bfs(g, n, source, desc=None, with_parent=True):
+    depth = torch.full((n,), 7777, dtype=torch.int32, device="cuda")
+    parent = torch.full((n,), 7777, dtype=torch.int32, device="cuda") if with_parent else None
+    gbx.bfs(g, source, depth, parent, desc if desc is not None else gbx.desc_init())
+    gbx.graph_sync(g)
+    return depth.cpu().numpy(), (parent.cpu().numpy() if with_parent else None)
+
+
+@pytest.mark.parametrize("name", ["rmat10", "rmat12-directed", "grid64", "er-directed"])
+def test_graph_build_matches_oracle_csr(name):
+    n, s, d, sym, og, g = graphs(name)
+    nn, nnz, gsym = g.info()
+    assert (nn, nnz, gsym) == (n, og.nnz, sym)
+    rp, col = gbx.graph_copy_csr(g, transpose=False)
+    assert np.array_equal(rp, og.out_ptr) and np.array_equal(col, og.out_col)
+    rp, col = gbx.graph_copy_csr(g, transpose=True)
+    assert np.array_equal(rp, og.in_ptr) and np.array_equal(col, og.in_col)
+
+
+def test_graph_build_keeps_self_loops_and_device_edges():
+    src = np.array([0, 1, 1, 2, 2, 0], np.int32)
+    dst = np.array([0, 1, 2, 0, 0, 0], np.int32)
+    g = gbx.graph_build(3, src, dst, symmetrize=False, drop_self_loops=False)
+    rp, col = gbx.graph_copy_csr(g)
+    want_rp, want_col = oracle.csr_build(3, src, dst, symmetrize=False, drop_self_loops=False)
+    assert np.array_equal(rp, want_rp) and np.array_equal(col, want_col)
+    gd = gbx.graph_build(3, torch.from_numpy(src).cuda(), torch.from_numpy(dst).cuda(), symmetrize=True)
+    rp, col = gbx.graph_copy_csr(gd)
+    want_rp, want_col = oracle.csr_build(3, src, dst)
+    assert np.array_equal(rp, want_rp) and np.array_equal(col, want_col)
+
+
+def test_graph_build_rejects_bad_index():
+    with pytest.raises(gbx.GbxError) as e:
+        gbx.graph_build(4, np.array([0, 9], np.int32), np.array([1, 2], np.int32))
+    assert e.value.status == gbx.ERR_INVALID_INDEX
+
+
+TOGGLES = list(itertools.product([gbx.DIR_AUTO, gbx.DIR_PUSH, gbx.DIR_PULL], [0, 1], [0, 1], [0, 1]))
+
+
+@pytest.mark.parametrize("direction,early_exit,masking,operand_reuse", TOGGLES)
+def test_bfs_rmat10_every_toggle(direction, early_exit, masking, operand_reuse):
+    n, s, d, sym, og, g = graphs("rmat10")
+    desc = gbx.desc_init(direction=direction, early_exit=early_exit, masking=masking, operand_reuse=operand_reuse)
+    for src in synth.sources(n, s, d, 4, seed=1):
+        want, _, _ = oracle.bfs(og, src)
+        depth, parent = run_bfs(g, n, int(src), desc)
+        assert np.array_equal(depth, want)
+        assert_valid_parents(og.out_ptr, og.out_col, depth, parent, src)
+
+
+@pytest.mark.parametrize("name", ["rmat14", "rmat12-directed", "grid64", "er-directed", "grid-exact"])
+@pytest.mark.parametrize("heuristic", [gbx.HEUR_RATIO, gbx.HEUR_BEAMER])
+def test_bfs_matches_oracle(name, heuristic):
+    n, s, d, sym, og, g = graphs(name)
+    desc = gbx.desc_init(heuristic=heuristic, alpha=0.01 if heuristic == gbx.HEUR_RATIO else 1 / 14)
+    for src in synth.sources(n, s, d, 6, seed=2):
+        want, _, _ = oracle.bfs(og, src)
+        depth, parent = run_bfs(g, n, int(src), desc)
+        assert np.array_equal(depth, want)
+        assert_valid_parents(og.out_ptr, og.out_col, depth, parent, src)
+
+
+def test_bfs_without_parent_output():
+    n, s, d, sym, og, g = graphs("rmat10")
+    src = int(synth.sources(n, s, d, 1, seed=5)[0])
+    depth, _ = run_bfs(g, n, src, with_parent=False)
+    assert np.array_equal(depth, oracle.bfs(og, src)[0])
+
+
+@pytest.mark.parametrize("name", ["rmat14", "rmat12-directed", "grid64"])
+@pytest.mark.parametrize("heuristic", [gbx.HEUR_RATIO, gbx.HEUR_BEAMER])
+def test_trace_matches_oracle_trace_and_schedule(name, heuristic):
+    n, s, d, sym, og, g = graphs(name)
+    alpha = 0.01 if heuristic == gbx.HEUR_RATIO else 1 / 14
+    for src in synth.sources(n, s, d, 3, seed=3):
+        want, _, levels = oracle.bfs(og, src)
+        otr = oracle.bfs_trace(og, want, levels)
+        sched = oracle.direction_schedule(otr, n, alpha=alpha, beta=0.01,
+                                          heuristic="ratio" if heuristic == gbx.HEUR_RATIO else "beamer")
+        desc = gbx.desc_init(heuristic=heuristic, alpha=alpha, trace=1)
+        depth, _ = run_bfs(g, n, int(src), desc)
+        assert np.array_equal(depth, want)
+        tr = gbx.bfs_trace(g)
+        assert len(tr) == levels
+        got_dirs = ["push" if x == gbx.DIR_PUSH else "pull" for x in tr["direction"]]
+        assert got_dirs == sched
+        for f in ["nf", "mf", "nu", "nu_nz", "mu", "n_new", "mf_new"]:
+            assert np.array_equal(tr[f], otr[f]), f
+        pull = tr["direction"] == gbx.DIR_PULL
+        assert np.array_equal(tr["e_exam"][pull], otr["e_exam"][pull])
+        assert np.all(tr["e_exam"][~pull] == -1)
+
+
+def test_trace_pull_only_matches_oracle_every_level():
+    n, s, d, sym, og, g = graphs("rmat14")
+    src = int(synth.sources(n, s, d, 1, seed=9)[0])
+    want, _, levels = oracle.bfs(og, src)
+    otr = oracle.bfs_trace(og, want, levels)
+    run_bfs(g, n, src, gbx.desc_init(direction=gbx.DIR_PULL, trace=1))
+    tr = gbx.bfs_trace(g)
+    assert np.array_equal(tr["e_exam"], otr["e_exam"])
+
+
+def test_edge_cases_isolated_source_empty_graph_single_vertex():
+    # isolated source: only itself is reached
+    src = np.array([1, 2], np.int32)
+    dst = np.array([2, 3], np.int32)
+    g = gbx.graph_build(6, src, dst)
+    depth, parent = run_bfs(g, 6, 5)
+    assert depth.tolist() == [-1, -1, -1, -1, -1, 0] and parent[5] == 5 and np.all(parent[:5] == -1)
+    # no edges at all
+    g0 = gbx.graph_build(70, np.zeros(0, np.int32), np.zeros(0, np.int32))
+    for direction in (gbx.DIR_AUTO, gbx.DIR_PUSH, gbx.DIR_PULL):
+        depth, _ = run_bfs(g0, 70, 33, gbx.desc_init(direction=direction))
+        assert depth[33] == 0 and np.sum(depth == -1) == 69
+    # one vertex
+    g1 = gbx.graph_build(1, np.zeros(0, np.int32), np.zeros(0, np.int32))
+    depth, parent = run_bfs(g1, 1, 0)
+    assert depth.tolist() == [0] and parent.tolist() == [0]
+    with pytest.raises(gbx.GbxError) as e:
+        run_bfs(g1, 1, 1)
+    assert e.value.status == gbx.ERR_INVALID_INDEX
+
+
+def test_long_path_many_levels():
+    n, s, d = synth.path_edges(5000)
+    g = gbx.graph_build(n, s, d)
+    for direction in (gbx.DIR_AUTO, gbx.DIR_PULL):
+        depth, parent = run_bfs(g, n, 1234, gbx.desc_init(direction=direction))
+        assert np.array_equal(depth, np.abs(np.arange(n) - 1234))
+        assert parent[1235] == 1234 and parent[1233] == 1234
+
+
+def test_repeat_runs_identical_depth():
+    n, s, d, sym, og, g = graphs("rmat14")
+    src = int(synth.sources(n, s, d, 1, seed=11)[0])
+    first, _ = run_bfs(g, n, src)
+    for _ in range(20):
+        again, _ = run_bfs(g, n, src)
+        assert np.array_equal(first, again)
+
+
+def test_bfs_host_buffers_match_device():
+    n, s, d, sym, og, g = graphs("rmat14")
+    srcs = synth.sources(n, s, d, 5, seed=13)
+    dh = torch.empty((len(srcs), n), dtype=torch.int32).pin_memory()
+    ph = torch.empty((len(srcs), n), dtype=torch.int32).pin_memory()
+    gbx.bfs_host(g, srcs, dh, ph)
+    for k, src in enumerate(srcs):
+        want, _, _ = oracle.bfs(og, src)
+        assert np.array_equal(dh[k].numpy(), want)
+        assert_valid_parents(og.out_ptr, og.out_col, dh[k].numpy(), ph[k].numpy(), src)
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    """Failure injection without a fault: a grid barrier one participant short
+    runs out of its (short) wait limit and records GBX_ERR_TIMEOUT; a BFS
+    launched while that error is pending returns at its first barrier; the host
+    reads the error through gbx_graph_sync, which clears it, and the next BFS
+    on the same context is correct."""
+    n, s, d, sym, og, g = graphs("rmat10")
+    src = int(synth.sources(n, s, d, 1, seed=1)[0])
+    gbx.selftest_barrier_timeout(g, 2_000_000)  # 2 ms
+    depth = torch.full((n,), 7777, dtype=torch.int32, device="cuda")
+    gbx.bfs(g, src, depth, None, gbx.desc_init())
+    with pytest.raises(gbx.GbxError) as e:
+        gbx.graph_sync(g)
+    assert e.value.status == gbx.ERR_TIMEOUT
+    gbx.graph_sync(g)  # cleared
+    depth2, _ = run_bfs(g, n, src)
+    assert np.array_equal(depth2, oracle.bfs(og, src)[0])
+
+
+@pytest.mark.slow
+def test_full_size_rmat22_sampled_sources():
+    """RMAT scale 22 (edge factor 16), in the launch configuration the benchmark
+    times: depths of sampled sources bit-exact against the oracle."""
+    n, s, d = synth.rmat_edges(22, 16, seed=1)
+    og = oracle.graph(n, s, d)
+    g = gbx.graph_build(n, s, d)
+    nn, nnz, _ = g.info()
+    assert nnz == og.nnz
+    srcs = synth.sources(n, s, d, 64, seed=1)
+    for src in list(srcs[:3]) + [int(srcs[-1])]:
+        want, _, levels = oracle.bfs(og, src)
+        depth, parent = run_bfs(g, n, int(src))
+        assert np.array_equal(depth, want)
+        # parents: check a seeded sample against the CSR
+        reached = np.flatnonzero(depth > 0)
+        pick = reached[np.random.default_rng(0).choice(len(reached), 2000, replace=False)]
+        assert np.all(depth[parent[pick]] == depth[pick] - 1)
+        for v in pick[:200]:
+            p = parent[v]
+            assert v in og.out_col[og.out_ptr[p]:og.out_ptr[p + 1]]
+    g.free()
+
+
+@pytest.mark.slow
+def test_full_size_grid2048():
+    n, s, d = synth.grid_edges(2048, 2048, p_delete=0.01, seed=1)
+    og = oracle.graph(n, s, d)
+    g = gbx.graph_build(n, s, d)
+    for src in synth.sources(n, s, d, 2, seed=1):
+        want, _, _ = oracle.bfs(og, src)
+        depth, _ = run_bfs(g, n, int(src))
+        assert np.array_equal(depth, want)
+    g.free()
