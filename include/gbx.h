@@ -233,6 +233,8 @@ typedef struct {
                           first hit (all of them without early exit); -1 on push levels */
     int64_t n_new;     /* |F_{L+1}| */
     int64_t mf_new;    /* out-edges of F_{L+1} */
+    int64_t time_ns;   /* device time of this level, barrier to barrier (%globaltimer); level 0
+                          includes the initialisation of depth, parent and the visited bitmap */
 } gbx_level;
 
 /* Copy the trace of the last traced BFS on g into levels[0..cap) and its

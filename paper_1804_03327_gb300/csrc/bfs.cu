@@ -26,9 +26,21 @@
 
 namespace gbx {
 
-constexpr int kBfsThreads = 256;
-constexpr int kBfsMinBlocks = 4;
-constexpr int kProbe = 16;  // in-neighbours one lane examines before the warp takes over the row
+#ifndef GBX_BFS_THREADS
+#define GBX_BFS_THREADS 512
+#endif
+#ifndef GBX_BFS_MIN_BLOCKS
+#define GBX_BFS_MIN_BLOCKS 2
+#endif
+#ifndef GBX_PUSH_ILP
+#define GBX_PUSH_ILP 2
+#endif
+#ifndef GBX_PULL_PROBE
+#define GBX_PULL_PROBE 16
+#endif
+constexpr int kBfsThreads = GBX_BFS_THREADS;
+constexpr int kBfsMinBlocks = GBX_BFS_MIN_BLOCKS;
+constexpr int kProbe = GBX_PULL_PROBE;  // in-neighbours one lane examines before the warp takes over the row
 enum { DIR_PUSH = GBX_DIR_PUSH, DIR_PULL = GBX_DIR_PULL };
 
 struct BfsArgs {
@@ -39,6 +51,7 @@ struct BfsArgs {
     const int32_t* in_ptr;
     const int32_t* in_col;
     const uint32_t* nz_in;
+    const int32_t* first_in;
     int32_t* depth;
     int32_t* parent;
     uint32_t* vis[2];
@@ -53,44 +66,109 @@ struct BfsArgs {
     float alpha, beta;
     int32_t heuristic, mode, early_exit, masking, operand_reuse, symmetric, need_indeg, trace_cap;
     unsigned long long timeout_ns;
+    unsigned int bar_parity;
 };
 
 struct Acc {
     unsigned long long n_new = 0, mf = 0, indeg = 0, exam = 0;
 };
 
-// Append the lanes with `take` to the next frontier queue.  One packed 64-bit
-// atomic per warp reserves both the queue slots and the out-degree prefix.
-__device__ __forceinline__ void warp_append(bool take, int32_t v, int32_t rs, int32_t od, LevelCtr* cout, int32_t* nq,
-                                            int32_t* nqp, int32_t* nqd) {
-    const uint32_t app = __ballot_sync(0xffffffffu, take);
-    if (!app) return;
-    const uint32_t inc = warp_inclusive_sum(take ? (uint32_t)od : 0u);
-    const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
-    unsigned long long old = 0;
-    if ((threadIdx.x & 31) == 0) old = atomicAdd(&cout->q, ((unsigned long long)tot << 32) | (unsigned long long)__popc(app));
-    old = __shfl_sync(0xffffffffu, old, 0);
-    if (take) {
-        const int32_t pos = (int32_t)(uint32_t)old + __popc(app & lanemask_lt());
-        const int32_t pre = (int32_t)(old >> 32) + (int32_t)(inc - (uint32_t)od);
-        nq[pos] = v;
-        nqp[pos] = pre;
-        nqd[pos] = rs - pre;
-    }
-}
+// Next-frontier appends are staged per warp in shared memory and published
+// kStage at a time: one packed 64-bit atomic reserves both the queue slots
+// (low 32 bits) and the matching range of the out-degree prefix (high 32
+// bits), so the prefix stays ascending in queue order and the queue needs no
+// separate scan.  Staging keeps same-address atomics on the level counter to
+// one per kStage discovered vertices.
+constexpr int kStage = 128;
+struct StageBuf {
+    int32_t v[kStage];
+};
 
-// Largest k in [0, count) with qp[k] <= e (qp ascending, qp[0] = 0).
-__device__ __forceinline__ int32_t find_entry(const int32_t* qp, int32_t count, long long e) {
-    int32_t lo = 0, hi = count - 1;
-    while (lo < hi) {
-        const int32_t mid = lo + ((hi - lo + 1) >> 1);
-        if ((long long)qp[mid] <= e)
-            lo = mid;
-        else
-            hi = mid - 1;
+struct Stage {
+    StageBuf* sb;
+    int cnt;  // warp-uniform
+    LevelCtr* cout;
+    int32_t* nq;
+    int32_t* nqp;
+    int32_t* nqd;
+    const int32_t* out_ptr;
+    const int32_t* in_ptr;
+    int count_degrees;  // add the staged vertices' degrees to acc (push levels)
+    int need_indeg;
+    Acc* acc;
+
+    // Publish the staged vertices: their row offsets are loaded here, all at once
+    // (off the per-edge critical path); vertices without out-edges are counted
+    // but not queued, so every queue entry owns at least one edge.
+    __device__ __forceinline__ void flush() {
+        if (cnt == 0) return;
+        __syncwarp();
+        const int lane = threadIdx.x & 31;
+        constexpr int R = kStage / 32;
+        int32_t v[R], rs[R], od[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            const int idx = t * 32 + lane;
+            v[t] = idx < cnt ? sb->v[idx] : -1;
+        }
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            rs[t] = v[t] >= 0 ? __ldg(out_ptr + v[t]) : 0;
+            od[t] = v[t] >= 0 ? __ldg(out_ptr + v[t] + 1) - rs[t] : 0;
+        }
+        if (count_degrees) {
+#pragma unroll
+            for (int t = 0; t < R; ++t) {
+                acc->mf += (unsigned long long)od[t];
+                if (need_indeg)
+                    acc->indeg += v[t] >= 0 ? (unsigned long long)(__ldg(in_ptr + v[t] + 1) - __ldg(in_ptr + v[t])) : 0ull;
+                else
+                    acc->indeg += (unsigned long long)od[t];
+            }
+        }
+        uint32_t keep[R];
+        uint32_t nkeep = 0, sum = 0;
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            keep[t] = __ballot_sync(0xffffffffu, od[t] > 0);
+            nkeep += __popc(keep[t]);
+            sum += (uint32_t)od[t];
+        }
+        if (nkeep > 0) {
+            const uint32_t tot = __reduce_add_sync(0xffffffffu, sum);
+            unsigned long long old = 0;
+            if (lane == 0) old = atomicAdd(&cout->q, ((unsigned long long)tot << 32) | (unsigned long long)nkeep);
+            old = __shfl_sync(0xffffffffu, old, 0);
+            int32_t pos = (int32_t)(uint32_t)old;
+            uint32_t pre_base = (uint32_t)(old >> 32);
+#pragma unroll
+            for (int t = 0; t < R; ++t) {
+                const uint32_t inc = warp_inclusive_sum((uint32_t)od[t]);
+                if (od[t] > 0) {
+                    const int32_t p = pos + __popc(keep[t] & lanemask_lt());
+                    const int32_t pre = (int32_t)(pre_base + inc - (uint32_t)od[t]);
+                    nq[p] = v[t];
+                    nqp[p] = pre;
+                    nqd[p] = rs[t] - pre;
+                }
+                pos += __popc(keep[t]);
+                pre_base += __shfl_sync(0xffffffffu, inc, 31);
+            }
+        }
+        cnt = 0;
+        __syncwarp();
     }
-    return lo;
-}
+
+    // Stage the lanes with `take` (all 32 lanes call this).
+    __device__ __forceinline__ void put(bool take, int32_t v) {
+        const uint32_t app = __ballot_sync(0xffffffffu, take);
+        if (!app) return;
+        if (cnt + __popc(app) > kStage) flush();
+        if (take) sb->v[cnt + __popc(app & lanemask_lt())] = v;
+        cnt += __popc(app);
+        __syncwarp();
+    }
+};
 
 __device__ __forceinline__ void flush_acc(const Acc& acc, LevelCtr* cout, bool with_exam) {
     const unsigned long long a = warp_sum_u64(acc.n_new);
@@ -107,192 +185,367 @@ __device__ __forceinline__ void flush_acc(const Acc& acc, LevelCtr* cout, bool w
 
 // ---------------------------------------------------------------- push (Eq 5)
 
-__device__ __forceinline__ void push_level(const BfsArgs& a, int32_t L, int cur, int vcur, uint32_t qcount,
-                                           uint32_t qedges, LevelCtr* cout, Acc& acc) {
+constexpr int kPushIlp = GBX_PUSH_ILP;  // edges per lane per step (independent chains)
+constexpr int kPushStep = 32 * kPushIlp;
+
+// Largest k in [0, count) with qp[k] <= e (qp ascending, qp[0] = 0), found by the
+// whole warp: 32 samples per round shrink the range 32-fold.
+__device__ __forceinline__ int32_t warp_find_entry(const int32_t* qp, int32_t count, long long e) {
     const int lane = threadIdx.x & 31;
+    int32_t lo = 0, hi = count;
+    while (hi - lo > 1) {
+        const long long span = hi - lo;
+        const int32_t idx = lo + (int32_t)((span * lane) >> 5);
+        const uint32_t m = __ballot_sync(0xffffffffu, (long long)qp[idx] <= e);
+        const int last = 31 - __clz(m);
+        const int32_t nlo = lo + (int32_t)((span * last) >> 5);
+        const int32_t nhi = last == 31 ? hi : lo + (int32_t)((span * (last + 1)) >> 5);
+        lo = nlo;
+        hi = nhi;
+    }
+    return lo;
+}
+
+// Edges of one push step: the frontier vertex u and child v of each lane's edges.
+struct PushStep {
+    int32_t u[kPushIlp];
+    int32_t v[kPushIlp];
+};
+
+// Walks a warp's edge range: maps edge ids to (queue entry, child) with a window
+// of the next 32 * kPushIlp entry boundaries (lane holds entries k+1+lane+32t).
+// Every entry has at least one edge, so the boundaries inside one step are all in
+// the window; it is reloaded only once a step could reach past its last boundary.
+struct PushCursor {
+    int32_t k;
+    int32_t wlast;
+    int32_t wv[kPushIlp];
+
+    __device__ __forceinline__ PushStep gather(const BfsArgs& a, const int32_t* q, const int32_t* qp,
+                                               const int32_t* qd, uint32_t qcount, int32_t base, int32_t e1) {
+        const int lane = threadIdx.x & 31;
+        if (wlast <= base + kPushStep - 1) {
+#pragma unroll
+            for (int t = 0; t < kPushIlp; ++t) {
+                const int32_t wi = k + 1 + lane + 32 * t;
+                wv[t] = wi < (int32_t)qcount ? qp[wi] : INT32_MAX;
+            }
+            wlast = __shfl_sync(0xffffffffu, wv[kPushIlp - 1], 31);
+        }
+        // occupancy of [base, base + kPushStep) by boundaries, one 32-bit word per lane-edge slot
+        uint32_t occ[kPushIlp];
+#pragma unroll
+        for (int m = 0; m < kPushIlp; ++m) {
+            uint32_t c = 0;
+#pragma unroll
+            for (int t = 0; t < kPushIlp; ++t) {
+                const int32_t rel = wv[t] - base;  // wv <= INT32_MAX, base >= 0: no overflow
+                c |= (rel >= 32 * m && rel < 32 * (m + 1)) ? (1u << (rel - 32 * m)) : 0u;
+            }
+            occ[m] = __reduce_or_sync(0xffffffffu, c);
+        }
+        PushStep st;
+        uint32_t before = 0;
+#pragma unroll
+        for (int t = 0; t < kPushIlp; ++t) {
+            const int32_t kk = k + (int32_t)(before + __popc(occ[t] & (0xffffffffu >> (31 - lane))));
+            before += __popc(occ[t]);
+            const int32_t e = base + 32 * t + lane;
+            st.u[t] = -1;
+            st.v[t] = 0;
+            if (e < e1) {
+                st.u[t] = q[kk];
+                st.v[t] = __ldg(a.out_col + (e + qd[kk]));
+            }
+        }
+        k += (int32_t)before;
+        return st;
+    }
+};
+
+__device__ __forceinline__ void push_level(const BfsArgs& a, int32_t L, int cur, int vcur, uint32_t qcount,
+                                           uint32_t qedges, Stage& stg, Acc& acc) {
     const int gwarp = (int)((blockIdx.x * kBfsThreads + threadIdx.x) >> 5);
     const int nwarps = (int)((gridDim.x * kBfsThreads) >> 5);
     const int32_t* q = a.q[cur];
     const int32_t* qp = a.qp[cur];
     const int32_t* qd = a.qd[cur];
-    int32_t* nq = a.q[cur ^ 1];
-    int32_t* nqp = a.qp[cur ^ 1];
-    int32_t* nqd = a.qd[cur ^ 1];
     uint32_t* vis = a.vis[vcur];
-    const long long E = qedges;
-    long long chunk = (E + nwarps - 1) / nwarps;
-    chunk = chunk < 64 ? 64 : ((chunk + 31) & ~31ll);
-    for (long long e0 = (long long)gwarp * chunk; e0 < E; e0 += (long long)nwarps * chunk) {
-        const long long e1 = e0 + chunk < E ? e0 + chunk : E;
-        int32_t k = 0;
-        if (lane == 0) k = find_entry(qp, (int32_t)qcount, e0);
-        k = __shfl_sync(0xffffffffu, k, 0);
-        for (long long base = e0; base < e1; base += 32) {
-            // queue entries whose edge ranges start inside [base, base + 32)
-            const int32_t wi = k + 1 + lane;
-            const long long bnd = wi < (int32_t)qcount ? (long long)qp[wi] : (long long)INT64_MAX;
-            const long long rel = bnd - base;
-            const uint32_t bits = __reduce_or_sync(0xffffffffu, (rel >= 0 && rel < 32) ? (1u << (int)rel) : 0u);
-            const long long e = base + lane;
-            bool claimed = false;
-            int32_t u = 0, v = 0;
-            if (e < e1) {
-                const int32_t kk = k + __popc(bits & (0xffffffffu >> (31 - lane)));
-                u = q[kk];
-                v = __ldg(a.out_col + (e + qd[kk]));
-                const uint32_t bit = 1u << (v & 31);
-                uint32_t* wp = vis + (v >> 5);
-                if (!(__ldcg(wp) & bit)) claimed = !(atomicOr(wp, bit) & bit);
+    const int32_t E = (int32_t)qedges;
+    int32_t chunk = (int32_t)(((long long)E + nwarps - 1) / nwarps);
+    chunk = chunk < kPushStep ? kPushStep : ((chunk + kPushStep - 1) / kPushStep) * kPushStep;
+    for (long long e0l = (long long)gwarp * chunk; e0l < E; e0l += (long long)nwarps * chunk) {
+        const int32_t e0 = (int32_t)e0l;
+        const int32_t e1 = E - e0 > chunk ? e0 + chunk : E;
+        PushCursor cur_;
+        cur_.k = warp_find_entry(qp, (int32_t)qcount, e0);
+        cur_.wlast = -1;
+        // two-stage pipeline: the children of step s + 1 are gathered (their loads in
+        // flight) while step s probes the visited bitmap and claims
+        PushStep now = cur_.gather(a, q, qp, qd, qcount, e0, e1);
+        for (int32_t base = e0; base < e1; base += kPushStep) {
+            PushStep nxt;
+            if (base + kPushStep < e1) {
+                nxt = cur_.gather(a, q, qp, qd, qcount, base + kPushStep, e1);
+            } else {
+#pragma unroll
+                for (int t = 0; t < kPushIlp; ++t) {
+                    nxt.u[t] = -1;
+                    nxt.v[t] = 0;
+                }
             }
-            int32_t rs = 0, od = 0;
-            if (claimed) {
-                a.depth[v] = L + 1;
-                if (a.parent) a.parent[v] = u;
-                rs = __ldg(a.out_ptr + v);
-                od = __ldg(a.out_ptr + v + 1) - rs;
-                acc.n_new += 1;
-                acc.mf += (unsigned long long)od;
-                if (a.need_indeg)
-                    acc.indeg += (unsigned long long)(__ldg(a.in_ptr + v + 1) - __ldg(a.in_ptr + v));
-                else
-                    acc.indeg += (unsigned long long)od;
+            uint32_t wd[kPushIlp];
+#pragma unroll
+            for (int t = 0; t < kPushIlp; ++t) wd[t] = now.u[t] >= 0 ? __ldca(vis + (now.v[t] >> 5)) : 0xffffffffu;
+            bool claimed[kPushIlp];
+#pragma unroll
+            for (int t = 0; t < kPushIlp; ++t) {
+                const uint32_t bit = 1u << (now.v[t] & 31);
+                // L1-cached probe: a stale word only costs an extra atomic, the atomic decides
+                claimed[t] = !(wd[t] & bit) && !(atomicOr(vis + (now.v[t] >> 5), bit) & bit);
             }
-            warp_append(claimed && od > 0, v, rs, od, cout, nq, nqp, nqd);
-            k += __popc(bits);
+#pragma unroll
+            for (int t = 0; t < kPushIlp; ++t) {
+                if (claimed[t]) {
+                    a.depth[now.v[t]] = L + 1;
+                    if (a.parent) a.parent[now.v[t]] = now.u[t];
+                    acc.n_new += 1;
+                }
+                stg.put(claimed[t], now.v[t]);
+            }
+            now = nxt;
         }
     }
+    stg.flush();
 }
 
 // ---------------------------------------------------------------- pull (Eq 4, Algorithm 2)
 
-__device__ __forceinline__ void pull_level(const BfsArgs& a, int32_t L, int cur, int vcur, bool use_fbm, bool append,
-                                           LevelCtr* cout, Acc& acc) {
+constexpr int kPullIlp = 2;  // candidate rows per lane per round (independent probe chains)
+
+// A warp takes a tile of 32 bitmap words (1024 vertices), finds the rows the
+// mask lets through (unvisited, with in-edges), packs them in registers
+// (per-word popcount, warp scan, __fns) and processes them 64 per round, two
+// rows per lane probing in lockstep; rows longer than kProbe are finished by
+// the whole warp.
+__device__ __forceinline__ void pull_level(const BfsArgs& a, int32_t L, int vcur, bool use_fbm, bool append,
+                                           Stage& st, uint32_t* snew, Acc& acc) {
     const int lane = threadIdx.x & 31;
     const int gwarp = (int)((blockIdx.x * kBfsThreads + threadIdx.x) >> 5);
     const int nwarps = (int)((gridDim.x * kBfsThreads) >> 5);
     const uint32_t* vprev = a.vis[vcur];
     uint32_t* vnext = a.vis[vcur ^ 1];
     const uint32_t* tbm = use_fbm ? a.fbm : vprev;
-    int32_t* nq = a.q[cur ^ 1];
-    int32_t* nqp = a.qp[cur ^ 1];
-    int32_t* nqd = a.qd[cur ^ 1];
-    for (int32_t w = gwarp; w < a.nwords; w += nwarps) {
-        const uint32_t cw = vprev[w];
-        const uint32_t nz = a.nz_in[w];
+    const int32_t ntiles = (a.nwords + 31) >> 5;
+    for (int32_t tile = gwarp; tile < ntiles; tile += nwarps) {
+        const int32_t w = (tile << 5) + lane;
+        const bool wok = w < a.nwords;
+        const uint32_t cw = wok ? vprev[w] : 0xffffffffu;
+        const uint32_t nz = wok ? a.nz_in[w] : 0u;
         const uint32_t cand = a.masking ? (~cw & nz) : nz;
-        if (cand == 0) {
-            if (lane == 0) vnext[w] = cw;
-            continue;
-        }
-        const int32_t i = (w << 5) + lane;
-        const bool mine = (cand >> lane) & 1u;
-        int32_t beg = 0, end = 0, k = 0, par = -1;
-        bool found = false, done = false;
-        unsigned long long exam = 0;
-        if (mine) {
-            beg = __ldg(a.in_ptr + i);
-            end = __ldg(a.in_ptr + i + 1);
-            k = beg;
-            const int32_t lim = end < beg + kProbe ? end : beg + kProbe;
-            while (k < lim) {
-                const int32_t cnt = lim - k < 4 ? lim - k : 4;
-                const int32_t j0 = __ldg(a.in_col + k);
-                const int32_t j1 = cnt > 1 ? __ldg(a.in_col + k + 1) : j0;
-                const int32_t j2 = cnt > 2 ? __ldg(a.in_col + k + 2) : j0;
-                const int32_t j3 = cnt > 3 ? __ldg(a.in_col + k + 3) : j0;
-                const bool h0 = bit_test(tbm, j0);
-                const bool h1 = cnt > 1 && bit_test(tbm, j1);
-                const bool h2 = cnt > 2 && bit_test(tbm, j2);
-                const bool h3 = cnt > 3 && bit_test(tbm, j3);
-                if (!found && (h0 | h1 | h2 | h3)) {
-                    const int hit = h0 ? 0 : (h1 ? 1 : (h2 ? 2 : 3));
-                    found = true;
-                    par = hit == 0 ? j0 : (hit == 1 ? j1 : (hit == 2 ? j2 : j3));
-                    if (a.early_exit) {
-                        exam += (unsigned long long)(hit + 1);
-                        k += hit + 1;
-                        done = true;
-                        break;
+        const uint32_t cntw = __popc(cand);
+        const uint32_t incl = warp_inclusive_sum(cntw);
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        const uint32_t excl = incl - cntw;
+        snew[lane] = 0u;
+        __syncwarp();
+        for (uint32_t base = 0; base < total; base += 32 * kPullIlp) {
+            bool mine[kPullIlp], found[kPullIlp], done[kPullIlp];
+            int jw[kPullIlp], bitpos[kPullIlp];
+            uint32_t cwj[kPullIlp];
+            int32_t i[kPullIlp], beg[kPullIlp], end[kPullIlp], k[kPullIlp], par[kPullIlp];
+            unsigned long long exam[kPullIlp];
+#pragma unroll
+            for (int r = 0; r < kPullIlp; ++r) {
+                const uint32_t c = base + 32 * r + lane;
+                mine[r] = c < total;
+                // word of candidate c: the largest j with excl_j <= c
+                int j = 0;
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1) {
+                    const uint32_t ev = __shfl_sync(0xffffffffu, excl, j + step);
+                    if (ev <= c) j += step;
+                }
+                jw[r] = j;
+                const uint32_t cj = __shfl_sync(0xffffffffu, cand, j);
+                const uint32_t ej = __shfl_sync(0xffffffffu, excl, j);
+                cwj[r] = __shfl_sync(0xffffffffu, cw, j);
+                bitpos[r] = mine[r] ? (int)__fns(cj, 0u, (int)(c - ej) + 1) : 0;
+                i[r] = (((tile << 5) + j) << 5) + bitpos[r];
+                found[r] = false;
+                done[r] = false;
+                par[r] = -1;
+                exam[r] = 0;
+            }
+            int32_t f0[kPullIlp];
+#pragma unroll
+            for (int r = 0; r < kPullIlp; ++r) {
+                beg[r] = mine[r] ? __ldg(a.in_ptr + i[r]) : 0;
+                end[r] = mine[r] ? __ldg(a.in_ptr + i[r] + 1) : 0;
+                f0[r] = mine[r] ? __ldg(a.first_in + i[r]) : -1;
+            }
+            // first probe from the dense first-neighbour array (same ascending order)
+#pragma unroll
+            for (int r = 0; r < kPullIlp; ++r) {
+                k[r] = beg[r];
+                if (f0[r] >= 0) {
+                    exam[r] = 1;
+                    k[r] = beg[r] + 1;
+                    if (bit_test(tbm, f0[r])) {
+                        found[r] = true;
+                        par[r] = f0[r];
+                        done[r] = a.early_exit != 0;
                     }
                 }
-                exam += (unsigned long long)cnt;
-                k += cnt;
             }
-        }
-        // rows longer than the lane probe: the whole warp scans them 32 at a time
-        uint32_t pend = __ballot_sync(0xffffffffu, mine && !done && k < end);
-        while (pend) {
-            const int t = __ffs(pend) - 1;
-            pend &= pend - 1;
-            int32_t kk = __shfl_sync(0xffffffffu, k, t);
-            const int32_t ee = __shfl_sync(0xffffffffu, end, t);
-            bool tf = __shfl_sync(0xffffffffu, found, t);
-            int32_t tp = __shfl_sync(0xffffffffu, par, t);
-            unsigned long long tx = 0;
-            for (; kk < ee; kk += 32) {
-                const int32_t idx = kk + lane;
-                const int32_t j = idx < ee ? __ldg(a.in_col + idx) : 0;
-                const uint32_t hb = __ballot_sync(0xffffffffu, idx < ee && bit_test(tbm, j));
-                if (hb) {
-                    const int f = __ffs(hb) - 1;
-                    const int32_t jf = __shfl_sync(0xffffffffu, j, f);
-                    if (!tf) {
-                        tf = true;
-                        tp = jf;
+            // lane probes: up to kProbe in-neighbours per row, four at a time, both rows in lockstep
+            for (int it = 0; it < kProbe / 4; ++it) {
+                int32_t jj[kPullIlp][4];
+                int32_t cnt[kPullIlp];
+                bool act[kPullIlp];
+#pragma unroll
+                for (int r = 0; r < kPullIlp; ++r) {
+                    const int32_t lim = end[r] < beg[r] + kProbe ? end[r] : beg[r] + kProbe;
+                    act[r] = mine[r] && !done[r] && k[r] < lim;
+                    cnt[r] = act[r] ? (lim - k[r] < 4 ? lim - k[r] : 4) : 0;
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) jj[r][t] = t < cnt[r] ? __ldg(a.in_col + k[r] + t) : 0;
+                }
+                if (!(act[0] || act[1])) break;
+#pragma unroll
+                for (int r = 0; r < kPullIlp; ++r) {
+                    if (!act[r]) continue;
+                    int hit = -1;
+#pragma unroll
+                    for (int t = 3; t >= 0; --t)
+                        if (t < cnt[r] && bit_test(tbm, jj[r][t])) hit = t;
+                    if (hit >= 0 && !found[r]) {
+                        found[r] = true;
+                        par[r] = jj[r][0];
+#pragma unroll
+                        for (int t = 1; t < 4; ++t)
+                            if (hit == t) par[r] = jj[r][t];
+                        if (a.early_exit) {
+                            exam[r] += (unsigned long long)(hit + 1);
+                            k[r] += hit + 1;
+                            done[r] = true;
+                            continue;
+                        }
                     }
-                    if (a.early_exit) {
-                        tx += (unsigned long long)(f + 1);
-                        break;
+                    exam[r] += (unsigned long long)cnt[r];
+                    k[r] += cnt[r];
+                }
+            }
+            // rows longer than the lane probe: the whole warp scans them 32 at a time
+#pragma unroll
+            for (int r = 0; r < kPullIlp; ++r) {
+                uint32_t pend = __ballot_sync(0xffffffffu, mine[r] && !done[r] && k[r] < end[r]);
+                while (pend) {
+                    const int t = __ffs(pend) - 1;
+                    pend &= pend - 1;
+                    int32_t kk = __shfl_sync(0xffffffffu, k[r], t);
+                    const int32_t ee = __shfl_sync(0xffffffffu, end[r], t);
+                    bool tf = __shfl_sync(0xffffffffu, found[r], t);
+                    int32_t tp = __shfl_sync(0xffffffffu, par[r], t);
+                    unsigned long long tx = 0;
+                    for (; kk < ee; kk += 32) {
+                        const int32_t idx = kk + lane;
+                        const int32_t j = idx < ee ? __ldg(a.in_col + idx) : 0;
+                        const uint32_t hb = __ballot_sync(0xffffffffu, idx < ee && bit_test(tbm, j));
+                        if (hb) {
+                            const int f = __ffs(hb) - 1;
+                            const int32_t jf = __shfl_sync(0xffffffffu, j, f);
+                            if (!tf) {
+                                tf = true;
+                                tp = jf;
+                            }
+                            if (a.early_exit) {
+                                tx += (unsigned long long)(f + 1);
+                                break;
+                            }
+                        }
+                        tx += (unsigned long long)(ee - kk < 32 ? ee - kk : 32);
+                    }
+                    if (lane == t) {
+                        found[r] = tf;
+                        par[r] = tp;
+                        exam[r] += tx;
                     }
                 }
-                tx += (unsigned long long)(ee - kk < 32 ? ee - kk : 32);
             }
-            if (lane == t) {
-                found = tf;
-                par = tp;
-                exam += tx;
+#pragma unroll
+            for (int r = 0; r < kPullIlp; ++r) {
+                // without masking a visited row may find a parent too; only unvisited rows are new
+                const bool isnew = found[r] && !((cwj[r] >> bitpos[r]) & 1u);
+                int32_t rs = 0, od = 0;
+                if (isnew) {
+                    atomicOr(snew + jw[r], 1u << bitpos[r]);
+                    a.depth[i[r]] = L + 1;
+                    if (a.parent) a.parent[i[r]] = par[r];
+                    if (a.symmetric) {
+                        rs = beg[r];
+                        od = end[r] - beg[r];
+                    } else {
+                        rs = __ldg(a.out_ptr + i[r]);
+                        od = __ldg(a.out_ptr + i[r] + 1) - rs;
+                    }
+                    acc.n_new += 1;
+                    acc.mf += (unsigned long long)od;
+                    acc.indeg += (unsigned long long)(end[r] - beg[r]);
+                }
+                acc.exam += exam[r];
+                if (append) st.put(isnew && od > 0, i[r]);
             }
         }
-        const uint32_t fmask = __ballot_sync(0xffffffffu, found);
-        const uint32_t newm = fmask & ~cw;
-        if (lane == 0) vnext[w] = cw | newm;
-        const bool isnew = (newm >> lane) & 1u;
-        int32_t rs = 0, od = 0;
-        if (isnew) {
-            a.depth[i] = L + 1;
-            if (a.parent) a.parent[i] = par;
-            if (a.symmetric) {
-                rs = beg;
-                od = end - beg;
-            } else {
-                rs = __ldg(a.out_ptr + i);
-                od = __ldg(a.out_ptr + i + 1) - rs;
-            }
-            acc.n_new += 1;
-            acc.mf += (unsigned long long)od;
-            acc.indeg += (unsigned long long)(end - beg);
-        }
-        acc.exam += exam;
-        if (append) warp_append(isnew && od > 0, i, rs, od, cout, nq, nqp, nqd);
+        __syncwarp();
+        if (wok) vnext[w] = cw | snew[lane];
+        __syncwarp();
     }
+    if (append) st.flush();
 }
 
 // DENSE2SPARSE at a pull -> push switch: F_{L+1} = visited now AND NOT visited before.
-__device__ __forceinline__ void bitmap_to_queue(const BfsArgs& a, int cur, int vcur, LevelCtr* cout) {
+__device__ __forceinline__ void bitmap_to_queue(const BfsArgs& a, int vcur, Stage& st) {
     const int lane = threadIdx.x & 31;
     const int gwarp = (int)((blockIdx.x * kBfsThreads + threadIdx.x) >> 5);
     const int nwarps = (int)((gridDim.x * kBfsThreads) >> 5);
-    for (int32_t w = gwarp; w < a.nwords; w += nwarps) {
-        const uint32_t nw = a.vis[vcur][w] & ~a.vis[vcur ^ 1][w];
-        if (!nw) continue;
-        const int32_t i = (w << 5) + lane;
-        const bool isnew = (nw >> lane) & 1u;
-        int32_t rs = 0, od = 0;
-        if (isnew) {
-            rs = __ldg(a.out_ptr + i);
-            od = __ldg(a.out_ptr + i + 1) - rs;
+    const int32_t ntiles = (a.nwords + 31) >> 5;
+    for (int32_t tile = gwarp; tile < ntiles; tile += nwarps) {
+        // lane l loads word tile*32 + l (coalesced), then the warp walks the nonempty words
+        const int32_t wl = (tile << 5) + lane;
+        const uint32_t mine = wl < a.nwords ? (a.vis[vcur][wl] & ~a.vis[vcur ^ 1][wl]) : 0u;
+        uint32_t todo = __ballot_sync(0xffffffffu, mine != 0u);
+        while (todo) {
+            const int j = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const uint32_t nw = __shfl_sync(0xffffffffu, mine, j);
+            st.put((nw >> lane) & 1u, (((tile << 5) + j) << 5) + lane);
         }
-        warp_append(isnew && od > 0, i, rs, od, cout, a.q[cur ^ 1], a.qp[cur ^ 1], a.qd[cur ^ 1]);
+    }
+    st.flush();
+}
+
+// out[i] = fill for all i < n except out[special] = special_value; 16-byte stores when aligned.
+__device__ __forceinline__ void fill_outputs(int32_t* out, int32_t n, int32_t fill, int32_t special,
+                                             int32_t special_value, long long gtid, long long gstride) {
+    if ((reinterpret_cast<uintptr_t>(out) & 15u) == 0) {
+        const long long n4 = n >> 2;
+        int4* o4 = reinterpret_cast<int4*>(out);
+        for (long long q = gtid; q < n4; q += gstride) {
+            int4 v = make_int4(fill, fill, fill, fill);
+            const long long b = q << 2;
+            if (special >= b && special < b + 4) {
+                const int r = (int)(special - b);
+                if (r == 0) v.x = special_value;
+                if (r == 1) v.y = special_value;
+                if (r == 2) v.z = special_value;
+                if (r == 3) v.w = special_value;
+            }
+            o4[q] = v;
+        }
+        for (long long i = (n4 << 2) + gtid; i < n; i += gstride) out[i] = i == special ? special_value : fill;
+    } else {
+        for (long long i = gtid; i < n; i += gstride) out[i] = i == special ? special_value : fill;
     }
 }
 
@@ -301,11 +554,10 @@ __global__ void __launch_bounds__(kBfsThreads, kBfsMinBlocks) bfs_kernel(BfsArgs
     const long long gtid = (long long)blockIdx.x * kBfsThreads + threadIdx.x;
     const long long gstride = (long long)gridDim.x * kBfsThreads;
     const int32_t s = a.source;
+    unsigned long long t_mark = kTrace && gtid == 0 ? global_timer_ns() : 0ull;
     // Algorithm 1, lines 2-5: f = e_s, v = {s}; outputs initialised
-    for (long long i = gtid; i < a.n; i += gstride) {
-        a.depth[i] = i == s ? 0 : -1;
-        if (a.parent) a.parent[i] = i == s ? s : -1;
-    }
+    fill_outputs(a.depth, a.n, -1, s, 0, gtid, gstride);
+    if (a.parent) fill_outputs(a.parent, a.n, -1, s, s, gtid, gstride);
     for (long long w = gtid; w < a.nwords; w += gstride) a.vis[0][w] = w == (s >> 5) ? 1u << (s & 31) : 0u;
     const int32_t s_rs = __ldg(a.out_ptr + s);
     const int32_t s_od = __ldg(a.out_ptr + s + 1) - s_rs;
@@ -324,46 +576,63 @@ __global__ void __launch_bounds__(kBfsThreads, kBfsMinBlocks) bfs_kernel(BfsArgs
         z.mf_new = (unsigned long long)s_od;
         a.ctr[0] = z;
         a.status[ST_LEVELS] = 0;
+        a.bar->count[a.bar_parity ^ 1u] = 0u;  // the next launch's counter
     }
-    if (!grid_barrier(a.bar, gridDim.x, a.status, a.timeout_ns)) return;
+    unsigned int* barc = a.bar->count + a.bar_parity;
+    unsigned int bar_round = 0;
+    if (!grid_barrier(barc, gridDim.x, bar_round, a.status, a.timeout_ns)) return;
 
+    __shared__ StageBuf stage_mem[kBfsThreads / 32];
+    __shared__ uint32_t tile_new[kBfsThreads / 32][32];
+    __shared__ unsigned long long lvl[5];  // counters of the level just finished, read once per block
+    const int wib = threadIdx.x >> 5;
+    unsigned long long qv = s_od > 0 ? (((unsigned long long)s_od << 32) | 1ull) : 0ull;
     int dir = a.mode == GBX_DIR_PULL ? DIR_PULL : DIR_PUSH;
     int cur = 0, vcur = 0;
     long long nf = 1, mf = s_od, mu = a.nnz - s_id;
     for (int32_t L = 0;; ++L) {
-        LevelCtr* cin = a.ctr + (L % 3);
         LevelCtr* cout = a.ctr + ((L + 1) % 3);
         if (gtid == 0) {
             LevelCtr z = {};
             a.ctr[(L + 2) % 3] = z;
         }
-        const unsigned long long qv = ld_volatile_u64(&cin->q);
         const uint32_t qcount = (uint32_t)qv, qedges = (uint32_t)(qv >> 32);
         Acc acc;
         bool appended;
+        Stage st{stage_mem + wib, 0, cout, a.q[cur ^ 1], a.qp[cur ^ 1], a.qd[cur ^ 1],
+                 a.out_ptr, a.in_ptr, dir == DIR_PUSH, a.need_indeg, &acc};
         if (dir == DIR_PUSH) {
-            push_level(a, L, cur, vcur, qcount, qedges, cout, acc);
+            push_level(a, L, cur, vcur, qcount, qedges, st, acc);
             appended = true;
         } else {
             const bool use_fbm = !a.operand_reuse;
             if (use_fbm) {
                 // frontier bitmap of F_L from its queue (vertices without out-edges cannot be parents)
                 for (long long w = gtid; w < a.nwords; w += gstride) a.fbm[w] = 0u;
-                if (!grid_barrier(a.bar, gridDim.x, a.status, a.timeout_ns)) return;
+                if (!grid_barrier(barc, gridDim.x, bar_round, a.status, a.timeout_ns)) return;
                 for (long long k = gtid; k < qcount; k += gstride) {
                     const int32_t v = a.q[cur][k];
                     atomicOr(a.fbm + (v >> 5), 1u << (v & 31));
                 }
-                if (!grid_barrier(a.bar, gridDim.x, a.status, a.timeout_ns)) return;
+                if (!grid_barrier(barc, gridDim.x, bar_round, a.status, a.timeout_ns)) return;
             }
             appended = use_fbm;
-            pull_level(a, L, cur, vcur, use_fbm, appended, cout, acc);
+            pull_level(a, L, vcur, use_fbm, appended, st, tile_new[wib], acc);
         }
         flush_acc(acc, cout, kTrace);
-        if (!grid_barrier(a.bar, gridDim.x, a.status, a.timeout_ns)) return;
-        const long long n_new = (long long)ld_volatile_u64(&cout->n_new);
-        const long long mf_new = (long long)ld_volatile_u64(&cout->mf_new);
-        const long long in_new = (long long)ld_volatile_u64(&cout->indeg_new);
+        if (!grid_barrier(barc, gridDim.x, bar_round, a.status, a.timeout_ns)) return;
+        if (threadIdx.x == 0) {
+            lvl[0] = ld_volatile_u64(&cout->n_new);
+            lvl[1] = ld_volatile_u64(&cout->mf_new);
+            lvl[2] = ld_volatile_u64(&cout->indeg_new);
+            lvl[3] = ld_volatile_u64(&cout->e_exam);
+            lvl[4] = ld_volatile_u64(&cout->q);
+        }
+        __syncthreads();
+        const long long n_new = (long long)lvl[0];
+        const long long mf_new = (long long)lvl[1];
+        const long long in_new = (long long)lvl[2];
+        qv = lvl[4];
         if (kTrace && gtid == 0 && L < a.trace_cap) {
             LevelRec r;
             r.direction = dir;
@@ -371,9 +640,12 @@ __global__ void __launch_bounds__(kBfsThreads, kBfsMinBlocks) bfs_kernel(BfsArgs
             r.nf = nf;
             r.mf = mf;
             r.mu = mu;
-            r.e_exam = dir == DIR_PULL ? (long long)ld_volatile_u64(&cout->e_exam) : -1;
+            r.e_exam = dir == DIR_PULL ? (long long)lvl[3] : -1;
             r.n_new = n_new;
             r.mf_new = mf_new;
+            const unsigned long long now = global_timer_ns();
+            r.t_ns = (long long)(now - t_mark);
+            t_mark = now;
             a.trace[L] = r;
         }
         if (n_new == 0) {
@@ -401,8 +673,11 @@ __global__ void __launch_bounds__(kBfsThreads, kBfsMinBlocks) bfs_kernel(BfsArgs
         }
         if (dir == DIR_PULL) vcur ^= 1;
         if (dir == DIR_PULL && next == DIR_PUSH && !appended) {
-            bitmap_to_queue(a, cur, vcur, cout);
-            if (!grid_barrier(a.bar, gridDim.x, a.status, a.timeout_ns)) return;
+            bitmap_to_queue(a, vcur, st);
+            if (!grid_barrier(barc, gridDim.x, bar_round, a.status, a.timeout_ns)) return;
+            if (threadIdx.x == 0) lvl[4] = ld_volatile_u64(&cout->q);
+            __syncthreads();
+            qv = lvl[4];
         }
         mu -= in_new;
         nf = n_new;
@@ -452,6 +727,7 @@ static gbx_status launch_bfs(Graph* G, int32_t source, int32_t* depth, int32_t* 
     a.in_ptr = G->in_ptr;
     a.in_col = G->in_col;
     a.nz_in = G->nz_in;
+    a.first_in = G->first_in;
     a.depth = depth;
     a.parent = parent;
     a.vis[0] = G->bm[0];
@@ -477,9 +753,11 @@ static gbx_status launch_bfs(Graph* G, int32_t source, int32_t* depth, int32_t* 
     a.need_indeg = (!G->symmetric && (d.trace || d.heuristic == GBX_HEUR_BEAMER)) ? 1 : 0;
     a.trace_cap = kTraceCap;
     a.timeout_ns = wait_timeout_ns();
+    a.bar_parity = G->bar_parity;
     void* args[] = {&a};
     const void* fn = d.trace ? (const void*)bfs_kernel<true> : (const void*)bfs_kernel<false>;
     GBX_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(G->bfs_blocks), dim3(kBfsThreads), args, 0, s));
+    G->bar_parity ^= 1u;
     G->last_stream = s;
     G->last_traced = d.trace ? 1 : 0;
     return GBX_OK;
@@ -491,8 +769,11 @@ using namespace gbx;
 
 namespace gbx {
 // One participant short: nobody ever completes the barrier, every block times out.
-__global__ void selftest_barrier_kernel(GridBar* bar, int32_t* status, unsigned long long timeout_ns) {
-    grid_barrier(bar, gridDim.x + 1, status, timeout_ns);
+__global__ void selftest_barrier_kernel(GridBar* bar, unsigned int parity, int32_t* status,
+                                        unsigned long long timeout_ns) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) bar->count[parity ^ 1u] = 0u;
+    unsigned int round = 0;
+    grid_barrier(bar->count + parity, gridDim.x + 1, round, status, timeout_ns);
 }
 }  // namespace gbx
 
@@ -500,7 +781,9 @@ extern "C" gbx_status gbx_selftest_barrier_timeout(gbx_graph* g, uint64_t timeou
     clear_error();
     GBX_TRY(check_graph(g));
     Graph* G = as_impl(g);
-    selftest_barrier_kernel<<<4, 32, 0, (cudaStream_t)stream>>>(G->bar, G->status, (unsigned long long)timeout_ns);
+    selftest_barrier_kernel<<<4, 32, 0, (cudaStream_t)stream>>>(G->bar, G->bar_parity, G->status,
+                                                                 (unsigned long long)timeout_ns);
+    G->bar_parity ^= 1u;
     GBX_CUDA_TRY(cudaGetLastError());
     G->last_stream = (cudaStream_t)stream;
     return GBX_OK;
@@ -627,6 +910,7 @@ extern "C" gbx_status gbx_bfs_trace(gbx_graph* g, gbx_level* levels, int32_t cap
         o.e_exam = r.e_exam;
         o.n_new = r.n_new;
         o.mf_new = r.mf_new;
+        o.time_ns = r.t_ns;
         levels[l] = o;
     }
     delete[] recs;

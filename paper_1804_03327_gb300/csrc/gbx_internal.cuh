@@ -58,9 +58,12 @@ struct LevelCtr {
     unsigned long long pad[3];
 };
 
+// Arrival counters of the persistent kernels' grid barrier.  Within one launch a
+// counter only grows (barrier r completes when it reaches r * nblocks); launches
+// alternate between the two counters and each launch zeroes the one it does not
+// use, so a launch that gave up half-way leaves nothing behind for the next.
 struct GridBar {
-    unsigned int count;
-    unsigned int gen;
+    unsigned int count[2];
     unsigned int pad[30];
 };
 
@@ -68,7 +71,7 @@ struct GridBar {
 struct LevelRec {
     int32_t direction;
     int32_t level;
-    long long nf, mf, mu, e_exam, n_new, mf_new;
+    long long nf, mf, mu, e_exam, n_new, mf_new, t_ns;
 };
 
 constexpr int kTraceCap = 1 << 16;
@@ -89,6 +92,10 @@ struct Graph {
     int32_t* in_col = nullptr;
     uint32_t* nz_in = nullptr;   // bit v set iff in-degree(v) > 0
     uint32_t* nz_out = nullptr;  // bit v set iff out-degree(v) > 0
+    // first (smallest) in-neighbour of each row, -1 if none: the first probe of a
+    // pull row reads this dense array instead of a random sector of in_col
+    int32_t* first_in = nullptr;
+    int32_t* first_out = nullptr;
     // scratch shared by the operations of this graph (ordered on one stream)
     uint32_t* bm[4] = {nullptr, nullptr, nullptr, nullptr};  // n-bit bitmaps
     int32_t* q[2] = {nullptr, nullptr};                       // frontier queues
@@ -109,6 +116,7 @@ struct Graph {
     cudaEvent_t ev_copied[2] = {nullptr, nullptr};
     // BFS launch geometry
     int bfs_blocks = 0;
+    unsigned int bar_parity = 0;  // counter of GridBar the next persistent launch uses
     cudaStream_t last_stream = nullptr;
     int last_traced = 0;
 };
@@ -184,40 +192,41 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x)
     return x;
 }
 
-// Grid-wide barrier for persistent cooperative kernels.  Bounded: a block that
-// waits longer than timeout_ns records GBX_ERR_TIMEOUT in status[ST_ERROR] and
-// every block returns false once any block has recorded an error.
-__device__ __forceinline__ bool grid_barrier(GridBar* bar, unsigned int nblocks, int32_t* status,
-                                             unsigned long long timeout_ns) {
+// Grid-wide barrier for persistent cooperative kernels.  Thread 0 of each block
+// arrives with a release reduction and polls with acquire loads until all
+// nblocks blocks of this round have arrived.  Bounded: a block that waits longer
+// than timeout_ns records GBX_ERR_TIMEOUT in status[ST_ERROR], and every block
+// returns false once any block has recorded an error (a block that sees a
+// pending error does not arrive).  `round` is thread 0's count of barriers
+// passed in this launch.
+__device__ __forceinline__ bool grid_barrier(unsigned int* count, unsigned int nblocks, unsigned int& round,
+                                             int32_t* status, unsigned long long timeout_ns) {
     __shared__ int ok_shared;
     __syncthreads();
-    if (threadIdx.x == 0 && ld_volatile_i32(status + ST_ERROR) != 0) {
-        ok_shared = 0;  // an error is pending: do not arrive, just leave
-    } else if (threadIdx.x == 0) {
+    if (threadIdx.x == 0) {
         int ok = 1;
-        const unsigned int gen = ld_acquire_u32(&bar->gen);
-        __threadfence();
-        const unsigned int arrived = atomicAdd(&bar->count, 1u);
-        if (arrived == nblocks - 1) {
-            atomicExch(&bar->count, 0u);
-            __threadfence();
-            atomicAdd(&bar->gen, 1u);
+        if (ld_volatile_i32(status + ST_ERROR) != 0) {
+            ok = 0;
         } else {
-            const unsigned long long t0 = global_timer_ns();
-            while (ld_acquire_u32(&bar->gen) == gen) {
-                if (ld_volatile_i32(status + ST_ERROR) != 0) {
-                    ok = 0;
-                    break;
-                }
-                if (global_timer_ns() - t0 > timeout_ns) {
-                    atomicCAS(status + ST_ERROR, 0, (int)GBX_ERR_TIMEOUT);
-                    ok = 0;
-                    break;
+            round += 1;
+            const unsigned int target = round * nblocks;
+            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
+            if ((int)(ld_acquire_u32(count) - target) < 0) {
+                const unsigned long long t0 = global_timer_ns();
+                while ((int)(ld_acquire_u32(count) - target) < 0) {
+                    if (ld_volatile_i32(status + ST_ERROR) != 0) {
+                        ok = 0;
+                        break;
+                    }
+                    if (global_timer_ns() - t0 > timeout_ns) {
+                        atomicCAS(status + ST_ERROR, 0, (int)GBX_ERR_TIMEOUT);
+                        ok = 0;
+                        break;
+                    }
                 }
             }
+            if (ok && ld_volatile_i32(status + ST_ERROR) != 0) ok = 0;
         }
-        if (ok && ld_volatile_i32(status + ST_ERROR) != 0) ok = 0;
-        __threadfence();
         ok_shared = ok;
     }
     __syncthreads();

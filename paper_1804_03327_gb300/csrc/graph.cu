@@ -70,6 +70,12 @@ __global__ void row_ptr_kernel(const int32_t* __restrict__ rows, int64_t nnz, in
     }
 }
 
+__global__ void first_neighbour_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                       int32_t n, int32_t* __restrict__ first) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        first[i] = row_ptr[i + 1] > row_ptr[i] ? col[row_ptr[i]] : -1;
+}
+
 __global__ void nonzero_rows_kernel(const int32_t* __restrict__ row_ptr, int32_t n, uint32_t* __restrict__ bm) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nw32 = ((int64_t)n + 31) & ~(int64_t)31;
@@ -145,6 +151,8 @@ static void graph_release(Graph* g) {
     f(g->out_col);
     f(g->nz_in);
     if (g->nz_out != g->nz_in) f(g->nz_out);
+    if (g->first_out != g->first_in) f(g->first_out);
+    f(g->first_in);
     for (auto& p : g->bm) f(p);
     for (int i = 0; i < 2; ++i) {
         f(g->q[i]);
@@ -268,6 +276,14 @@ static gbx_status build_impl(Graph* g, int32_t n, int64_t m, const int32_t* src,
     } else {
         GBX_CUDA_TRY(cudaMalloc((void**)&g->nz_out, sizeof(uint32_t) * ((size_t)g->nwords + 1)));
         nonzero_rows_kernel<<<div_up(nw32, 256), 256, 0, s>>>(g->out_ptr, n, g->nz_out);
+    }
+    GBX_CUDA_TRY(cudaMalloc((void**)&g->first_in, sizeof(int32_t) * ((size_t)n + 1)));
+    first_neighbour_kernel<<<grid_for(n), 256, 0, s>>>(g->in_ptr, g->in_col, n, g->first_in);
+    if (sym) {
+        g->first_out = g->first_in;
+    } else {
+        GBX_CUDA_TRY(cudaMalloc((void**)&g->first_out, sizeof(int32_t) * ((size_t)n + 1)));
+        first_neighbour_kernel<<<grid_for(n), 256, 0, s>>>(g->out_ptr, g->out_col, n, g->first_out);
     }
     GBX_CUDA_TRY(cudaGetLastError());
     GBX_CUDA_TRY(cudaStreamSynchronize(s));

@@ -72,10 +72,11 @@ class Desc(ctypes.Structure):
 class Level(ctypes.Structure):
     _fields_ = [("direction", ctypes.c_int32), ("level", ctypes.c_int32), ("nf", ctypes.c_int64),
                 ("mf", ctypes.c_int64), ("nu", ctypes.c_int64), ("nu_nz", ctypes.c_int64), ("mu", ctypes.c_int64),
-                ("e_exam", ctypes.c_int64), ("n_new", ctypes.c_int64), ("mf_new", ctypes.c_int64)]
+                ("e_exam", ctypes.c_int64), ("n_new", ctypes.c_int64), ("mf_new", ctypes.c_int64),
+                ("time_ns", ctypes.c_int64)]
 
 
-LEVEL_FIELDS = ["direction", "level", "nf", "mf", "nu", "nu_nz", "mu", "e_exam", "n_new", "mf_new"]
+LEVEL_FIELDS = ["direction", "level", "nf", "mf", "nu", "nu_nz", "mu", "e_exam", "n_new", "mf_new", "time_ns"]
 
 
 def lib_path() -> str:
