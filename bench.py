@@ -53,7 +53,33 @@ def parse():
     p.add_argument("--scale", type=int, default=SCALE)
     p.add_argument("--cpu-sample", type=int, default=8, help="sources the CPU oracle baseline times")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--probe", type=int, default=None, metavar="K",
+                   help="profiling aid: run only source K of the workload --repeat times (for ncu -k bfs_kernel)")
+    p.add_argument("--repeat", type=int, default=5)
     return p.parse_args()
+
+
+def run_probe(args):
+    """Build the workload's graph and run BFS from its K-th source `repeat` times
+    (the last launch is the one a profiler capture with -s repeat-1 -c 1 sees)."""
+    import torch
+
+    import synth
+    from paper_1804_03327_gb300 import gbx, roofline
+
+    gbx.load()
+    n, src, dst = synth.rmat_edges(args.scale, EDGE_FACTOR, seed=SEED)
+    s = int(rank_sources(n, src, dst, 0)[args.probe])
+    g = gbx.graph_build(n, src, dst)
+    depth = torch.empty(n, dtype=torch.int32, device="cuda")
+    parent = torch.empty(n, dtype=torch.int32, device="cuda")
+    for _ in range(args.repeat):
+        gbx.bfs(g, s, depth, parent, gbx.desc_init())
+    gbx.graph_sync(g)
+    gbx.bfs(g, s, depth, parent, gbx.desc_init(trace=1))
+    tr = gbx.bfs_trace(g)
+    print(json.dumps({"probe_source": s, "algorithmic_bytes": roofline.bfs_bytes(tr, n),
+                      "reached_edges": roofline.reached_edges(tr), **roofline.summary(tr)}))
 
 
 def dist_env():
@@ -108,7 +134,7 @@ def ncu_traffic(scale: int):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -123,7 +149,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -364,7 +390,9 @@ def run_ours(args):
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.probe is not None:
+        run_probe(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
