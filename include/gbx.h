@@ -192,6 +192,36 @@ gbx_status gbx_mxv(gbx_vector* w, const gbx_vector* mask, int32_t semiring, cons
  * output pointer may be NULL. */
 gbx_status gbx_mxv_stats(const gbx_graph* A, int64_t* rows, int64_t* examined, int64_t* u_nnz, int64_t* edges);
 
+/*
+ * Allocation-free variant of the pull (row-based) matvec, for callers that
+ * cannot allocate device memory when they call in: a serving process whose
+ * device memory is all preallocated by its own pool, a latency-bound loop that
+ * must not pay for the device-wide synchronisation cudaMalloc/cudaFree can
+ * cause, or an embedding that forbids allocation after start-up.  The paper
+ * has no counterpart to this entry point.
+ * Computes, like gbx_mxv with direction PULL, transpose 0 and accum 0:
+ *   w(i) = pass(i) ? OR over j in row i of (u(j) != 0) : 0,
+ *   pass(i) = (mask(i) != 0, or 1 when mask is NULL) XOR mask_complement,
+ * stopping each row at its first hit when early_exit is set (same result).
+ * The matrix is given as caller-owned device CSR arrays row_ptr (int32[n+1]) and
+ * col (int32[row_ptr[n]], values in [0, n)); pass the CSR of A^T (for example
+ * from gbx_graph_csr with transpose = 1) to compute A^T u as BFS does.
+ * u, mask (may be NULL) and w are device uint8_t[n]; w must not alias u or mask.
+ * Scratch: four n-bit bitmaps in one fixed device array inside the library, so
+ * n is limited to 16777216 (larger n returns GBX_ERR_INVALID_VALUE); the array
+ * (8 MiB) stays allocated on every GPU that loads the library until exit.  No
+ * cudaMalloc, cudaFree or allocating library routine is called.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress with
+ * that device current); make that first call before any stream capture.  All
+ * calls share the array: calls whose work overlaps on the GPU (different
+ * streams, or concurrent host threads) race and must be ordered by the caller.
+ * Each call rewrites every scratch word it reads.  Asynchronous on `stream`.
+ * Errors: INVALID_VALUE, NULL_POINTER, NOT_SUPPORTED (device index >= 64), CUDA.
+ */
+gbx_status gbx_mxv_pull_noalloc(int32_t n, const int32_t* row_ptr, const int32_t* col, const uint8_t* u,
+                                const uint8_t* mask, int32_t mask_complement, int32_t early_exit, uint8_t* w,
+                                void* stream);
+
 /* ------------------------------------------------------------------ BFS */
 
 /*

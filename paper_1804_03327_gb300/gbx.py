@@ -48,6 +48,7 @@ EXPORTED = [
     "gbx_last_error", "gbx_status_string", "gbx_version", "gbx_graph_build", "gbx_graph_free", "gbx_graph_info",
     "gbx_graph_csr", "gbx_graph_copy_csr", "gbx_graph_sync", "gbx_desc_init", "gbx_mxv", "gbx_mxv_stats",
     "gbx_bfs", "gbx_bfs_host", "gbx_bfs_trace", "gbx_set_wait_timeout_ns", "gbx_selftest_barrier_timeout",
+    "gbx_mxv_pull_noalloc",
 ]
 
 
@@ -113,6 +114,7 @@ def load():
                 "gbx_bfs_trace": (ctypes.c_int, [p, ctypes.POINTER(Level), i32, ctypes.POINTER(i32)]),
                 "gbx_set_wait_timeout_ns": (ctypes.c_int, [u64]),
                 "gbx_selftest_barrier_timeout": (ctypes.c_int, [p, u64, p]),
+                "gbx_mxv_pull_noalloc": (ctypes.c_int, [i32, p, p, p, p, i32, i32, p, p]),
             }
             for name, (res, args) in sigs.items():
                 fn = getattr(L, name)
@@ -262,6 +264,22 @@ def mxv_stats(A: Graph):
     vals = [ctypes.c_int64() for _ in range(4)]
     _check(load().gbx_mxv_stats(A.handle, *[ctypes.byref(v) for v in vals]), "gbx_mxv_stats")
     return dict(zip(["rows", "examined", "u_nnz", "edges"], [v.value for v in vals]))
+
+
+def graph_csr(g: Graph, transpose: bool = False):
+    """Device pointers (row_ptr, col) of A (or A^T), owned by the graph."""
+    rp, col = ctypes.c_void_p(), ctypes.c_void_p()
+    _check(load().gbx_graph_csr(g.handle, int(transpose), ctypes.byref(rp), ctypes.byref(col)), "gbx_graph_csr")
+    return rp.value, col.value
+
+
+def mxv_pull_noalloc(n: int, row_ptr: int, col: int, u, mask, w, mask_complement: bool = False,
+                     early_exit: bool = True, stream=None):
+    """Allocation-free pull matvec on caller-owned CSR (device addresses) and
+    CUDA uint8 tensors u, mask (or None) and w."""
+    _check(load().gbx_mxv_pull_noalloc(int(n), row_ptr, col, u.data_ptr(),
+                                       mask.data_ptr() if mask is not None else None, int(mask_complement),
+                                       int(early_exit), w.data_ptr(), _stream_ptr(stream)), "gbx_mxv_pull_noalloc")
 
 
 def bfs(g: Graph, source: int, depth, parent=None, desc: Desc | None = None, stream=None):
