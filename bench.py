@@ -108,7 +108,7 @@ def peaks():
 
 def kernel_source_sha() -> str:
     h = hashlib.sha256()
-    for f in ["bfs.cu", "gbx_internal.cuh"]:
+    for f in ["bfs.cu", "frontier.cuh", "gbx_internal.cuh"]:
         with open(os.path.join(ROOT, "paper_1804_03327_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -271,6 +271,36 @@ typedef struct {
  * length into *nlevels.  Synchronises the graph's last BFS stream. */
 gbx_status gbx_bfs_trace(gbx_graph* g, gbx_level* levels, int32_t cap, int32_t* nlevels);
 
+/* Depth element types of gbx_bfs_batch. */
+#define GBX_DEPTH_I32 0
+#define GBX_DEPTH_I16 1 /* a depth of 32767 or more fails with GBX_ERR_OVERFLOW */
+
+/*
+ * Batched multi-source BFS: S independent BFS runs (Algorithm 1 for each source)
+ * carried together as bit lanes -- lane b of vertex v is one bit of a uint64
+ * word, and the Boolean semiring acts lane-wise (OR = bitwise OR over words).
+ * Every level runs push (Eq 5 lane-wise, 64-bit atomicOr into the next words) or
+ * pull (Eq 4 lane-wise: masking by the unvisited lanes, early exit once every
+ * unvisited lane of a vertex has a parent, operand reuse) for the whole batch;
+ * with desc->direction = AUTO the device picks pull when the active vertices'
+ * out-edges exceed desc->alpha * nnz, else push.  Sources may repeat.
+ * sources: host int32[S] in [0, n).  depth: device buffer [S][n] of int32
+ * (GBX_DEPTH_I32) or int16 (GBX_DEPTH_I16): depth[b][v] = hops from sources[b],
+ * -1 if unreached -- each row equals gbx_bfs from that source.  Scratch (3 x n x
+ * ceil(S/64) uint64) is allocated on the first call and kept by the graph.
+ * Asynchronous on `stream`; device-side errors are reported by gbx_graph_sync.
+ * Errors: NULL_POINTER, INVALID_VALUE (S < 1, depth_type, desc), INVALID_INDEX,
+ * OUT_OF_MEMORY, CUDA.
+ */
+gbx_status gbx_bfs_batch(gbx_graph* g, const int32_t* sources, int32_t S, void* depth, int32_t depth_type,
+                         const gbx_desc* desc, void* stream);
+
+/* Per-level records of the last gbx_bfs_batch on g (synchronises): direction,
+ * nf = active vertices, mf = their out-edges, mu = (vertex, lane) pairs found at
+ * the previous level, e_exam = edges examined by pull levels (once per 256-lane
+ * chunk), n_new = pairs found at this level, mf_new, time_ns; nu and nu_nz are -1. */
+gbx_status gbx_bfs_batch_trace(gbx_graph* g, gbx_level* levels, int32_t cap, int32_t* nlevels);
+
 /* Upper bound, in nanoseconds, of every device-side wait in this library (the
  * persistent kernels' grid barriers).  When it runs out the kernel records
  * GBX_ERR_TIMEOUT and returns.  Default 5e9.  Process-wide. */

@@ -1,0 +1,194 @@
+// Frontier machinery shared by the single-source and the batched BFS kernels:
+// per-level counters, the staged frontier queue with its out-degree prefix, and
+// the edge-balanced cursor that walks a queue's edges.
+#pragma once
+
+#include "gbx_internal.cuh"
+
+#ifndef GBX_PUSH_ILP
+#define GBX_PUSH_ILP 2
+#endif
+
+namespace gbx {
+
+constexpr int kPushIlp = GBX_PUSH_ILP;  // edges per lane per push step (independent chains)
+constexpr int kPushStep = 32 * kPushIlp;
+
+struct Acc {
+    unsigned long long n_new = 0, mf = 0, indeg = 0, exam = 0;
+};
+
+// Next-frontier appends are staged per warp in shared memory and published
+// kStage at a time: one packed 64-bit atomic reserves both the queue slots
+// (low 32 bits) and the matching range of the out-degree prefix (high 32
+// bits), so the prefix stays ascending in queue order and the queue needs no
+// separate scan.  Staging keeps same-address atomics on the level counter to
+// one per kStage discovered vertices.
+constexpr int kStage = 128;
+struct StageBuf {
+    int32_t v[kStage];
+};
+
+struct Stage {
+    StageBuf* sb;
+    int cnt;  // warp-uniform
+    LevelCtr* cout;
+    int32_t* nq;
+    int32_t* nqp;
+    int32_t* nqd;
+    const int32_t* out_ptr;
+    const int32_t* in_ptr;
+    int count_degrees;  // add the staged vertices' degrees to acc (push levels)
+    int need_indeg;
+    Acc* acc;
+
+    // Publish the staged vertices: their row offsets are loaded here, all at once
+    // (off the per-edge critical path); vertices without out-edges are counted
+    // but not queued, so every queue entry owns at least one edge.
+    __device__ __forceinline__ void flush() {
+        if (cnt == 0) return;
+        __syncwarp();
+        const int lane = threadIdx.x & 31;
+        constexpr int R = kStage / 32;
+        int32_t v[R], rs[R], od[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            const int idx = t * 32 + lane;
+            v[t] = idx < cnt ? sb->v[idx] : -1;
+        }
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            rs[t] = v[t] >= 0 ? __ldg(out_ptr + v[t]) : 0;
+            od[t] = v[t] >= 0 ? __ldg(out_ptr + v[t] + 1) - rs[t] : 0;
+        }
+        if (count_degrees) {
+#pragma unroll
+            for (int t = 0; t < R; ++t) {
+                acc->mf += (unsigned long long)od[t];
+                if (need_indeg)
+                    acc->indeg += v[t] >= 0 ? (unsigned long long)(__ldg(in_ptr + v[t] + 1) - __ldg(in_ptr + v[t])) : 0ull;
+                else
+                    acc->indeg += (unsigned long long)od[t];
+            }
+        }
+        uint32_t keep[R];
+        uint32_t nkeep = 0, sum = 0;
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            keep[t] = __ballot_sync(0xffffffffu, od[t] > 0);
+            nkeep += __popc(keep[t]);
+            sum += (uint32_t)od[t];
+        }
+        if (nkeep > 0) {
+            const uint32_t tot = __reduce_add_sync(0xffffffffu, sum);
+            unsigned long long old = 0;
+            if (lane == 0) old = atomicAdd(&cout->q, ((unsigned long long)tot << 32) | (unsigned long long)nkeep);
+            old = __shfl_sync(0xffffffffu, old, 0);
+            int32_t pos = (int32_t)(uint32_t)old;
+            uint32_t pre_base = (uint32_t)(old >> 32);
+#pragma unroll
+            for (int t = 0; t < R; ++t) {
+                const uint32_t inc = warp_inclusive_sum((uint32_t)od[t]);
+                if (od[t] > 0) {
+                    const int32_t p = pos + __popc(keep[t] & lanemask_lt());
+                    const int32_t pre = (int32_t)(pre_base + inc - (uint32_t)od[t]);
+                    nq[p] = v[t];
+                    nqp[p] = pre;
+                    nqd[p] = rs[t] - pre;
+                }
+                pos += __popc(keep[t]);
+                pre_base += __shfl_sync(0xffffffffu, inc, 31);
+            }
+        }
+        cnt = 0;
+        __syncwarp();
+    }
+
+    // Stage the lanes with `take` (all 32 lanes call this).
+    __device__ __forceinline__ void put(bool take, int32_t v) {
+        const uint32_t app = __ballot_sync(0xffffffffu, take);
+        if (!app) return;
+        if (cnt + __popc(app) > kStage) flush();
+        if (take) sb->v[cnt + __popc(app & lanemask_lt())] = v;
+        cnt += __popc(app);
+        __syncwarp();
+    }
+};
+
+// Largest k in [0, count) with qp[k] <= e (qp ascending, qp[0] = 0), found by the
+// whole warp: 32 samples per round shrink the range 32-fold.
+__device__ __forceinline__ int32_t warp_find_entry(const int32_t* qp, int32_t count, long long e) {
+    const int lane = threadIdx.x & 31;
+    int32_t lo = 0, hi = count;
+    while (hi - lo > 1) {
+        const long long span = hi - lo;
+        const int32_t idx = lo + (int32_t)((span * lane) >> 5);
+        const uint32_t m = __ballot_sync(0xffffffffu, (long long)qp[idx] <= e);
+        const int last = 31 - __clz(m);
+        const int32_t nlo = lo + (int32_t)((span * last) >> 5);
+        const int32_t nhi = last == 31 ? hi : lo + (int32_t)((span * (last + 1)) >> 5);
+        lo = nlo;
+        hi = nhi;
+    }
+    return lo;
+}
+
+// Edges of one push step: the frontier vertex u and child v of each lane's edges.
+struct PushStep {
+    int32_t u[kPushIlp];
+    int32_t v[kPushIlp];
+};
+
+// Walks a warp's edge range: maps edge ids to (queue entry, child) with a window
+// of the next 32 * kPushIlp entry boundaries (lane holds entries k+1+lane+32t).
+// Every entry has at least one edge, so the boundaries inside one step are all in
+// the window; it is reloaded only once a step could reach past its last boundary.
+struct PushCursor {
+    int32_t k;
+    int32_t wlast;
+    int32_t wv[kPushIlp];
+
+    __device__ __forceinline__ PushStep gather(const int32_t* out_col, const int32_t* q, const int32_t* qp,
+                                               const int32_t* qd, uint32_t qcount, int32_t base, int32_t e1) {
+        const int lane = threadIdx.x & 31;
+        if (wlast <= base + kPushStep - 1) {
+#pragma unroll
+            for (int t = 0; t < kPushIlp; ++t) {
+                const int32_t wi = k + 1 + lane + 32 * t;
+                wv[t] = wi < (int32_t)qcount ? qp[wi] : INT32_MAX;
+            }
+            wlast = __shfl_sync(0xffffffffu, wv[kPushIlp - 1], 31);
+        }
+        // occupancy of [base, base + kPushStep) by boundaries, one 32-bit word per lane-edge slot
+        uint32_t occ[kPushIlp];
+#pragma unroll
+        for (int m = 0; m < kPushIlp; ++m) {
+            uint32_t c = 0;
+#pragma unroll
+            for (int t = 0; t < kPushIlp; ++t) {
+                const int32_t rel = wv[t] - base;  // wv <= INT32_MAX, base >= 0: no overflow
+                c |= (rel >= 32 * m && rel < 32 * (m + 1)) ? (1u << (rel - 32 * m)) : 0u;
+            }
+            occ[m] = __reduce_or_sync(0xffffffffu, c);
+        }
+        PushStep st;
+        uint32_t before = 0;
+#pragma unroll
+        for (int t = 0; t < kPushIlp; ++t) {
+            const int32_t kk = k + (int32_t)(before + __popc(occ[t] & (0xffffffffu >> (31 - lane))));
+            before += __popc(occ[t]);
+            const int32_t e = base + 32 * t + lane;
+            st.u[t] = -1;
+            st.v[t] = 0;
+            if (e < e1) {
+                st.u[t] = q[kk];
+                st.v[t] = __ldg(out_col + (e + qd[kk]));
+            }
+        }
+        k += (int32_t)before;
+        return st;
+    }
+};
+
+
+}  // namespace gbx

@@ -117,6 +117,16 @@ struct Graph {
     // BFS launch geometry
     int bfs_blocks = 0;
     unsigned int bar_parity = 0;  // counter of GridBar the next persistent launch uses
+    // batched multi-source BFS scratch (allocated on first use, grown as needed)
+    unsigned long long* msV = nullptr;  // visited lanes [n][W]
+    unsigned long long* msF = nullptr;  // lanes found at the current level [n][W]
+    unsigned long long* msN = nullptr;  // push accumulation [n][W]
+    int64_t ms_cap_words = 0;
+    int32_t* ms_src = nullptr;       // device copy of the sources
+    int32_t* ms_src_pinned = nullptr;
+    int32_t ms_src_cap = 0;
+    int ms_blocks = 0;
+    cudaEvent_t ms_src_ready = nullptr;
     cudaStream_t last_stream = nullptr;
     int last_traced = 0;
 };

@@ -170,6 +170,12 @@ static void graph_release(Graph* g) {
     f(g->trace);
     f(g->status);
     f(g->flag);
+    f(g->msV);
+    f(g->msF);
+    f(g->msN);
+    f(g->ms_src);
+    if (g->ms_src_pinned) cudaFreeHost(g->ms_src_pinned);
+    if (g->ms_src_ready) cudaEventDestroy(g->ms_src_ready);
     if (g->copy_stream) cudaStreamDestroy(g->copy_stream);
     delete g;
 }

@@ -1,0 +1,634 @@
+// Batched multi-source BFS: S sources at once as bit lanes (Algorithm 1 run for
+// S frontier vectors together), with the Boolean semiring acting lane-wise on
+// uint64 words (OR = bitwise OR, AND = bitwise AND).  Lane b of vertex v is
+// bit b % 64 of word b / 64 of v's W-word row.
+//
+// State (vertex-major, W words per vertex, W padded to a multiple of the chunk):
+//   V[v]  lanes in which v has been visited,
+//   F[v]  lanes in which v was found at the previous level (valid for vertices on
+//         the active list),
+//   N[v]  push accumulator (zero outside the level's touched vertices),
+//   D     one bit per vertex: every lane visited (pull skips it without loads).
+// Each level runs in the direction chosen for the whole batch:
+//   push (Eq 5 lane-wise): the active list's edges are split evenly over warps;
+//     each edge ORs F[u] into N[v] (64-bit atomics, only nonzero words); the
+//     vertices touched first are listed, then finalised: new = N & ~V.
+//   pull (Eq 4 lane-wise, masking + early exit + operand reuse): every vertex with
+//     an unvisited lane ORs V of its in-neighbours (V is the state before this
+//     level) and stops as soon as every unvisited lane is covered; new = acc & ~V.
+// New lanes get depth L + 1; depth writes are transposed through the warp so that
+// 32 consecutive vertices of one lane are one coalesced store.
+#include "frontier.cuh"
+#include "gbx_internal.cuh"
+
+namespace gbx {
+
+constexpr int kMsThreads = 512;
+constexpr int kMsProbe = 8;  // in-neighbours a lane scans alone before the warp takes over
+
+struct MsArgs {
+    int32_t n, S, W, nwords;
+    long long nnz;
+    const int32_t* out_ptr;
+    const int32_t* out_col;
+    const int32_t* in_ptr;
+    const int32_t* in_col;
+    const uint32_t* nz_in;
+    unsigned long long* V;
+    unsigned long long* F;
+    unsigned long long* N;
+    uint32_t* D;        // all lanes visited
+    uint32_t* T;        // touched by the current push level
+    int32_t* tlist;     // touched vertices
+    void* depth;        // [S][n]
+    int depth16;
+    const int32_t* src;
+    int32_t* q[2];
+    int32_t* qp[2];
+    int32_t* qd[2];
+    LevelCtr* ctr;
+    GridBar* bar;
+    unsigned int bar_parity;
+    LevelRec* trace;
+    int32_t* status;
+    float alpha;
+    int32_t mode, trace_cap, symmetric;
+    unsigned long long timeout_ns;
+};
+
+__device__ __forceinline__ unsigned long long lane_mask(int32_t S, int32_t w) {
+    const int32_t lo = w * 64;
+    if (lo + 64 <= S) return ~0ull;
+    if (lo >= S) return 0ull;
+    return (1ull << (S - lo)) - 1ull;
+}
+
+__device__ __forceinline__ void store_depth(const MsArgs& a, int32_t lane_b, int32_t v, int32_t d) {
+    const size_t idx = (size_t)lane_b * (size_t)a.n + (size_t)v;
+    if (a.depth16)
+        static_cast<int16_t*>(a.depth)[idx] = (int16_t)d;
+    else
+        static_cast<int32_t*>(a.depth)[idx] = d;
+}
+
+// Depth writes for one word of new lanes, transposed through the warp: for each
+// lane bit set anywhere in the warp, the lanes holding it store together.
+__device__ __forceinline__ void write_depth_word(const MsArgs& a, int32_t w, unsigned long long nw, int32_t v,
+                                                 int32_t d) {
+    const uint32_t lo = __reduce_or_sync(0xffffffffu, (uint32_t)nw);
+    const uint32_t hi = __reduce_or_sync(0xffffffffu, (uint32_t)(nw >> 32));
+    uint32_t m = lo;
+    while (m) {
+        const int b = __ffs(m) - 1;
+        m &= m - 1;
+        if ((nw >> b) & 1ull) store_depth(a, w * 64 + b, v, d);
+    }
+    m = hi;
+    while (m) {
+        const int b = __ffs(m) - 1;
+        m &= m - 1;
+        if ((nw >> (32 + b)) & 1ull) store_depth(a, w * 64 + 32 + b, v, d);
+    }
+}
+
+// ---------------------------------------------------------------- pull level
+
+template <int CW>
+__device__ __forceinline__ void ms_pull(const MsArgs& a, int32_t L, Stage& st, Acc& acc) {
+    const int lane = threadIdx.x & 31;
+    const int gwarp = (int)((blockIdx.x * kMsThreads + threadIdx.x) >> 5);
+    const int nwarps = (int)((gridDim.x * kMsThreads) >> 5);
+    const int32_t ntiles = (a.n + 31) >> 5;
+    for (int32_t tile = gwarp; tile < ntiles; tile += nwarps) {
+        const int32_t v = (tile << 5) + lane;
+        const uint32_t todo = v < a.n ? (a.nz_in[tile] & ~a.D[tile]) : 0u;
+        if (__ballot_sync(0xffffffffu, (todo >> lane) & 1u) == 0u) continue;
+        const bool mine = (todo >> lane) & 1u;
+        int32_t beg = 0, end = 0;
+        bool sink = false;
+        if (mine) {
+            beg = __ldg(a.in_ptr + v);
+            end = __ldg(a.in_ptr + v + 1);
+            sink = !a.symmetric && __ldg(a.out_ptr + v + 1) == __ldg(a.out_ptr + v);
+        }
+        // A vertex without out-edges is nobody's in-neighbour, so no other row reads
+        // its V during this level: its new lanes are committed in place (it never
+        // joins the active list, which holds vertices with out-edges only).
+        bool any_new = false, full = true;
+        for (int32_t c = 0; c < a.W; c += CW) {
+            unsigned long long unv[CW], accw[CW];
+            bool pend = false;
+#pragma unroll
+            for (int j = 0; j < CW; ++j) {
+                unv[j] = mine ? (~a.V[(size_t)v * a.W + c + j] & lane_mask(a.S, c + j)) : 0ull;
+                accw[j] = 0ull;
+                pend |= unv[j] != 0ull;
+            }
+            unsigned long long exam = 0;
+            // lane probes: up to kMsProbe in-neighbours, two loads in flight
+            int32_t k = beg;
+            bool covered = !pend;
+            const int32_t lim = end < beg + kMsProbe ? end : beg + kMsProbe;
+            while (!covered && k < lim) {
+                const bool two = k + 1 < lim;
+                const int32_t u0 = __ldg(a.in_col + k);
+                const int32_t u1 = two ? __ldg(a.in_col + k + 1) : u0;
+                covered = true;
+#pragma unroll
+                for (int j = 0; j < CW; ++j) {
+                    accw[j] |= a.V[(size_t)u0 * a.W + c + j] | a.V[(size_t)u1 * a.W + c + j];
+                    covered &= (accw[j] & unv[j]) == unv[j];
+                }
+                k += two ? 2 : 1;
+                exam += two ? 2u : 1u;
+            }
+            // long rows: the whole warp ORs 32 in-neighbours at a time and stops once
+            // every unvisited lane of the chunk is covered (warp OR-reduction)
+            uint32_t wpend = __ballot_sync(0xffffffffu, !covered && k < end);
+            while (wpend) {
+                const int t = __ffs(wpend) - 1;
+                wpend &= wpend - 1;
+                const int32_t kt = __shfl_sync(0xffffffffu, k, t);
+                const int32_t et = __shfl_sync(0xffffffffu, end, t);
+                unsigned long long ut[CW], wa[CW];
+#pragma unroll
+                for (int j = 0; j < CW; ++j) {
+                    ut[j] = __shfl_sync(0xffffffffu, unv[j], t);
+                    wa[j] = __shfl_sync(0xffffffffu, accw[j], t);
+                }
+                unsigned long long tx = 0;
+                for (int32_t kk = kt; kk < et; kk += 32) {
+                    const int32_t idx = kk + lane;
+                    unsigned long long x[CW];
+                    if (idx < et) {
+                        const int32_t u = __ldg(a.in_col + idx);
+#pragma unroll
+                        for (int j = 0; j < CW; ++j) x[j] = a.V[(size_t)u * a.W + c + j];
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < CW; ++j) x[j] = 0ull;
+                    }
+                    bool cov = true;
+#pragma unroll
+                    for (int j = 0; j < CW; ++j) {
+                        const uint32_t lo = __reduce_or_sync(0xffffffffu, (uint32_t)x[j]);
+                        const uint32_t hi = __reduce_or_sync(0xffffffffu, (uint32_t)(x[j] >> 32));
+                        wa[j] |= ((unsigned long long)hi << 32) | lo;
+                        cov &= (wa[j] & ut[j]) == ut[j];
+                    }
+                    tx += (unsigned long long)(et - kk < 32 ? et - kk : 32);
+                    if (cov) break;
+                }
+                if (lane == t) {
+#pragma unroll
+                    for (int j = 0; j < CW; ++j) accw[j] = wa[j];
+                    exam += tx;
+                }
+            }
+            acc.exam += exam;
+#pragma unroll
+            for (int j = 0; j < CW; ++j) {
+                const unsigned long long nw = accw[j] & unv[j];
+                if (mine) a.F[(size_t)v * a.W + c + j] = nw;
+                if (sink) {
+                    a.V[(size_t)v * a.W + c + j] |= nw;
+                    full &= unv[j] == nw;
+                }
+                any_new |= nw != 0ull;
+                acc.n_new += (unsigned long long)__popcll(nw);
+                write_depth_word(a, c + j, nw, v, L + 1);
+            }
+        }
+        if (sink && full) atomicOr(a.D + (v >> 5), 1u << (v & 31));
+        st.put(any_new && !sink, v);
+    }
+    st.flush();
+}
+
+// V |= F for the vertices found by the pull level; mark vertices with all lanes visited.
+template <int CW>
+__device__ __forceinline__ void ms_pull_commit(const MsArgs& a, const int32_t* list, uint32_t count) {
+    const long long gtid = (long long)blockIdx.x * kMsThreads + threadIdx.x;
+    const long long gstride = (long long)gridDim.x * kMsThreads;
+    for (long long k = gtid; k < count; k += gstride) {
+        const int32_t v = list[k];
+        bool full = true;
+        for (int32_t w = 0; w < a.W; ++w) {
+            const unsigned long long x = a.V[(size_t)v * a.W + w] | a.F[(size_t)v * a.W + w];
+            a.V[(size_t)v * a.W + w] = x;
+            full &= (x & lane_mask(a.S, w)) == lane_mask(a.S, w);
+        }
+        if (full) atomicOr(a.D + (v >> 5), 1u << (v & 31));
+    }
+}
+
+// ---------------------------------------------------------------- push level
+
+template <int CW>
+__device__ __forceinline__ void ms_push_scatter(const MsArgs& a, int cur, uint32_t qcount, uint32_t qedges,
+                                                LevelCtr* cout) {
+    const int lane = threadIdx.x & 31;
+    const int gwarp = (int)((blockIdx.x * kMsThreads + threadIdx.x) >> 5);
+    const int nwarps = (int)((gridDim.x * kMsThreads) >> 5);
+    const int32_t* q = a.q[cur];
+    const int32_t* qp = a.qp[cur];
+    const int32_t* qd = a.qd[cur];
+    const int32_t E = (int32_t)qedges;
+    int32_t chunk = (int32_t)(((long long)E + nwarps - 1) / nwarps);
+    chunk = chunk < kPushStep ? kPushStep : ((chunk + kPushStep - 1) / kPushStep) * kPushStep;
+    for (long long e0l = (long long)gwarp * chunk; e0l < E; e0l += (long long)nwarps * chunk) {
+        const int32_t e0 = (int32_t)e0l;
+        const int32_t e1 = E - e0 > chunk ? e0 + chunk : E;
+        PushCursor cur_;
+        cur_.k = warp_find_entry(qp, (int32_t)qcount, e0);
+        cur_.wlast = -1;
+        for (int32_t base = e0; base < e1; base += kPushStep) {
+            const PushStep ps = cur_.gather(a.out_col, q, qp, qd, qcount, base, e1);
+#pragma unroll
+            for (int t = 0; t < kPushIlp; ++t) {
+                const int32_t u = ps.u[t], v = ps.v[t];
+                bool touched = false;
+                if (u >= 0 && !((a.D[v >> 5] >> (v & 31)) & 1u)) {
+                    for (int32_t c = 0; c < a.W; c += CW) {
+#pragma unroll
+                        for (int j = 0; j < CW; ++j) {
+                            const unsigned long long f = a.F[(size_t)u * a.W + c + j];
+                            if (f) {
+                                atomicOr(a.N + (size_t)v * a.W + c + j, f);
+                                touched = true;
+                            }
+                        }
+                    }
+                }
+                bool first = false;
+                if (touched) first = !(atomicOr(a.T + (v >> 5), 1u << (v & 31)) & (1u << (v & 31)));
+                // warp-aggregated append to the touched list
+                const uint32_t m = __ballot_sync(0xffffffffu, first);
+                if (m) {
+                    unsigned long long base_pos = 0;
+                    if (lane == 0) base_pos = atomicAdd(&cout->pad[0], (unsigned long long)__popc(m));
+                    base_pos = __shfl_sync(0xffffffffu, base_pos, 0);
+                    if (first) a.tlist[base_pos + __popc(m & lanemask_lt())] = v;
+                }
+            }
+        }
+    }
+}
+
+// new = N & ~V for the touched vertices; V |= new, F = new, N = 0, depth.
+template <int CW>
+__device__ __forceinline__ void ms_push_finalize(const MsArgs& a, int32_t L, uint32_t count, Stage& st, Acc& acc) {
+    const long long gtid = (long long)blockIdx.x * kMsThreads + threadIdx.x;
+    const long long gstride = (long long)gridDim.x * kMsThreads;
+    const long long rounds = ((long long)count + gstride - 1) / gstride;
+    for (long long r = 0; r < rounds; ++r) {  // warp-uniform trip count: st.put needs all lanes
+        const long long k = r * gstride + gtid;
+        const bool mine = k < count;
+        const int32_t v = mine ? a.tlist[k] : 0;
+        bool any_new = false, full = true;
+        for (int32_t w = 0; w < a.W; ++w) {
+            unsigned long long nw = 0;
+            if (mine) {
+                const size_t idx = (size_t)v * a.W + w;
+                const unsigned long long nn = a.N[idx];
+                const unsigned long long vv = a.V[idx];
+                nw = nn & ~vv & lane_mask(a.S, w);
+                a.V[idx] = vv | nw;
+                a.F[idx] = nw;
+                a.N[idx] = 0ull;
+                full &= ((vv | nw) & lane_mask(a.S, w)) == lane_mask(a.S, w);
+                acc.n_new += (unsigned long long)__popcll(nw);
+                any_new |= nw != 0ull;
+            }
+            unsigned long long m = nw;
+            while (m) {
+                const int b = __ffsll((long long)m) - 1;
+                m &= m - 1;
+                store_depth(a, w * 64 + b, v, L + 1);
+            }
+        }
+        if (mine) {
+            atomicAnd(a.T + (v >> 5), ~(1u << (v & 31)));
+            if (full) atomicOr(a.D + (v >> 5), 1u << (v & 31));
+        }
+        st.put(mine && any_new, v);
+    }
+    st.flush();
+}
+
+// ---------------------------------------------------------------- kernel
+
+template <int CW>
+__global__ void __launch_bounds__(kMsThreads, 1) ms_bfs_kernel(MsArgs a) {
+    const long long gtid = (long long)blockIdx.x * kMsThreads + threadIdx.x;
+    const long long gstride = (long long)gridDim.x * kMsThreads;
+    __shared__ StageBuf stage_mem[kMsThreads / 32];
+    __shared__ unsigned long long lvl[6];
+    const int wib = threadIdx.x >> 5;
+    unsigned int* barc = a.bar->count + a.bar_parity;
+    unsigned int bar_round = 0;
+    unsigned long long t_mark = gtid == 0 ? global_timer_ns() : 0ull;
+    // ---- init: V = N = 0, D = T = 0, depth = -1
+    const size_t nw_total = (size_t)a.n * (size_t)a.W;
+    for (size_t i = gtid; i < nw_total; i += gstride) {
+        a.V[i] = 0ull;
+        a.N[i] = 0ull;
+    }
+    for (long long w = gtid; w < a.nwords; w += gstride) {
+        a.D[w] = 0u;
+        a.T[w] = 0u;
+    }
+    const size_t nd = (size_t)a.S * (size_t)a.n;
+    if (a.depth16) {
+        int16_t* d = static_cast<int16_t*>(a.depth);
+        for (size_t i = gtid; i < nd; i += gstride) d[i] = (int16_t)-1;
+    } else {
+        int32_t* d = static_cast<int32_t*>(a.depth);
+        for (size_t i = gtid; i < nd; i += gstride) d[i] = -1;
+    }
+    if (gtid == 0) {
+        LevelCtr z = {};
+        a.ctr[0] = z;
+        a.ctr[1] = z;
+        a.ctr[2] = z;
+        a.status[ST_LEVELS] = 0;
+        a.bar->count[a.bar_parity ^ 1u] = 0u;
+    }
+    if (!grid_barrier(barc, gridDim.x, bar_round, a.status, a.timeout_ns)) return;
+    // ---- sources: lane b starts at src[b] with depth 0
+    for (long long b = gtid; b < a.S; b += gstride) {
+        const int32_t s = a.src[b];
+        atomicOr(a.V + (size_t)s * a.W + (b >> 6), 1ull << (b & 63));
+        store_depth(a, (int32_t)b, s, 0);
+    }
+    if (!grid_barrier(barc, gridDim.x, bar_round, a.status, a.timeout_ns)) return;
+    // F = V for the (distinct) source vertices; they form the first active list
+    {
+        Acc acc0;
+        Stage st{stage_mem + wib, 0, a.ctr + 0, a.q[0], a.qp[0], a.qd[0], a.out_ptr, a.in_ptr, 1, 0, &acc0};
+        const long long rounds = ((long long)a.S + gstride - 1) / gstride;
+        for (long long r = 0; r < rounds; ++r) {
+            const long long b = r * gstride + gtid;
+            bool take = false;
+            int32_t s = 0;
+            if (b < a.S) {
+                s = a.src[b];
+                take = !(atomicOr(a.T + (s >> 5), 1u << (s & 31)) & (1u << (s & 31)));
+                if (take)
+                    for (int32_t w = 0; w < a.W; ++w) a.F[(size_t)s * a.W + w] = a.V[(size_t)s * a.W + w];
+            }
+            st.put(take, s);
+        }
+        st.flush();
+        const unsigned long long m = warp_sum_u64(acc0.mf);
+        if ((threadIdx.x & 31) == 0 && m) atomicAdd(&a.ctr[0].mf_new, m);
+    }
+    if (!grid_barrier(barc, gridDim.x, bar_round, a.status, a.timeout_ns)) return;
+    for (long long b = gtid; b < a.S; b += gstride) {
+        const int32_t s = a.src[b];
+        a.T[s >> 5] = 0u;  // racing writers all store zero
+    }
+    if (threadIdx.x == 0) lvl[4] = ld_volatile_u64(&a.ctr[0].q);
+    if (!grid_barrier(barc, gridDim.x, bar_round, a.status, a.timeout_ns)) return;
+    unsigned long long qv = lvl[4];
+    int cur = 0;
+    long long pairs = a.S;
+    for (int32_t L = 0;; ++L) {
+        LevelCtr* cout = a.ctr + ((L + 1) % 3);
+        if (gtid == 0) {
+            LevelCtr z = {};
+            a.ctr[(L + 2) % 3] = z;
+        }
+        const uint32_t qcount = (uint32_t)qv, qedges = (uint32_t)(qv >> 32);
+        // direction for the whole batch: pull once the active edges exceed alpha * nnz
+        int dir = a.mode;
+        if (dir == GBX_DIR_AUTO) dir = (double)qedges > (double)a.alpha * (double)a.nnz ? GBX_DIR_PULL : GBX_DIR_PUSH;
+        if (a.depth16 && L + 1 > 32767) {
+            if (gtid == 0) atomicCAS(a.status + ST_ERROR, 0, (int)GBX_ERR_OVERFLOW);
+            return;
+        }
+        Acc acc;
+        Stage st{stage_mem + wib, 0, cout, a.q[cur ^ 1], a.qp[cur ^ 1], a.qd[cur ^ 1], a.out_ptr, a.in_ptr, 1, 0, &acc};
+        if (dir == GBX_DIR_PUSH) {
+            ms_push_scatter<CW>(a, cur, qcount, qedges, cout);
+            if (!grid_barrier(barc, gridDim.x, bar_round, a.status, a.timeout_ns)) return;
+            if (threadIdx.x == 0) lvl[5] = ld_volatile_u64(&cout->pad[0]);
+            __syncthreads();
+            ms_push_finalize<CW>(a, L, (uint32_t)lvl[5], st, acc);
+        } else {
+            ms_pull<CW>(a, L, st, acc);
+        }
+        {
+            const unsigned long long x = warp_sum_u64(acc.n_new);
+            const unsigned long long y = warp_sum_u64(acc.mf);
+            const unsigned long long z = warp_sum_u64(acc.exam);
+            if ((threadIdx.x & 31) == 0) {
+                if (x) atomicAdd(&cout->n_new, x);
+                if (y) atomicAdd(&cout->mf_new, y);
+                if (z) atomicAdd(&cout->e_exam, z);
+            }
+        }
+        if (!grid_barrier(barc, gridDim.x, bar_round, a.status, a.timeout_ns)) return;
+        if (threadIdx.x == 0) {
+            lvl[0] = ld_volatile_u64(&cout->n_new);
+            lvl[1] = ld_volatile_u64(&cout->mf_new);
+            lvl[3] = ld_volatile_u64(&cout->e_exam);
+            lvl[4] = ld_volatile_u64(&cout->q);
+            lvl[5] = ld_volatile_u64(&cout->pad[0]);
+        }
+        __syncthreads();
+        qv = lvl[4];
+        if (dir == GBX_DIR_PULL) {
+            // V |= F for the vertices the pull found (their new lanes were kept apart so the
+            // level read V as it was before it started)
+            ms_pull_commit<CW>(a, a.q[cur ^ 1], (uint32_t)qv);
+            if (!grid_barrier(barc, gridDim.x, bar_round, a.status, a.timeout_ns)) return;
+        }
+        const long long n_new = (long long)lvl[0];
+        if (gtid == 0 && L < a.trace_cap) {
+            LevelRec r;
+            r.direction = dir;
+            r.level = L;
+            r.nf = (long long)qcount;
+            r.mf = (long long)qedges;
+            r.mu = pairs;
+            r.e_exam = dir == GBX_DIR_PULL ? (long long)lvl[3] : -1;
+            r.n_new = n_new;
+            r.mf_new = (long long)lvl[1];
+            const unsigned long long now = global_timer_ns();
+            r.t_ns = (long long)(now - t_mark);
+            t_mark = now;
+            a.trace[L] = r;
+        }
+        if (n_new == 0) {
+            if (gtid == 0) a.status[ST_LEVELS] = L + 1;
+            return;
+        }
+        if (L + 1 >= a.n) {
+            if (gtid == 0) atomicCAS(a.status + ST_ERROR, 0, (int)GBX_ERR_OVERFLOW);
+            return;
+        }
+        pairs = n_new;
+        cur ^= 1;
+    }
+}
+
+static gbx_status ms_reserve(Graph* G, int32_t W, int32_t S, cudaStream_t s) {
+    const int64_t need = (int64_t)G->n * W;
+    if (G->ms_cap_words < need) {
+        if (G->msV) {
+            GBX_CUDA_TRY(cudaStreamSynchronize(s));
+            cudaFree(G->msV);
+            cudaFree(G->msF);
+            cudaFree(G->msN);
+            G->msV = G->msF = G->msN = nullptr;
+            G->ms_cap_words = 0;
+        }
+        GBX_CUDA_TRY(cudaMalloc((void**)&G->msV, sizeof(unsigned long long) * (size_t)need));
+        GBX_CUDA_TRY(cudaMalloc((void**)&G->msF, sizeof(unsigned long long) * (size_t)need));
+        GBX_CUDA_TRY(cudaMalloc((void**)&G->msN, sizeof(unsigned long long) * (size_t)need));
+        G->ms_cap_words = need;
+    }
+    if (G->ms_src_cap < S) {
+        if (G->ms_src) {
+            GBX_CUDA_TRY(cudaStreamSynchronize(s));
+            cudaFree(G->ms_src);
+            cudaFreeHost(G->ms_src_pinned);
+            G->ms_src = nullptr;
+            G->ms_src_pinned = nullptr;
+        }
+        GBX_CUDA_TRY(cudaMalloc((void**)&G->ms_src, sizeof(int32_t) * (size_t)S));
+        GBX_CUDA_TRY(cudaMallocHost((void**)&G->ms_src_pinned, sizeof(int32_t) * (size_t)S));
+        G->ms_src_cap = S;
+    }
+    if (!G->ms_src_ready) GBX_CUDA_TRY(cudaEventCreateWithFlags(&G->ms_src_ready, cudaEventDisableTiming));
+    return GBX_OK;
+}
+
+template <int CW>
+static gbx_status ms_launch(Graph* G, const MsArgs& a0, cudaStream_t s) {
+    int per_sm = 0;
+    GBX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ms_bfs_kernel<CW>, kMsThreads, 0));
+    GBX_CHECK(per_sm >= 1, GBX_ERR_CUDA, "batched BFS kernel cannot be resident");
+    MsArgs a = a0;
+    void* args[] = {&a};
+    GBX_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)ms_bfs_kernel<CW>, dim3(per_sm * G->num_sms),
+                                             dim3(kMsThreads), args, 0, s));
+    return GBX_OK;
+}
+
+}  // namespace gbx
+
+using namespace gbx;
+
+extern "C" gbx_status gbx_bfs_batch(gbx_graph* g, const int32_t* sources, int32_t S, void* depth, int32_t depth_type,
+                                    const gbx_desc* desc, void* stream) {
+    clear_error();
+    GBX_TRY(check_graph(g));
+    Graph* G = as_impl(g);
+    GBX_CHECK(S >= 1, GBX_ERR_INVALID_VALUE, "S must be >= 1");
+    GBX_CHECK(sources != nullptr && depth != nullptr, GBX_ERR_NULL_POINTER, "sources or depth is NULL");
+    GBX_CHECK(depth_type == GBX_DEPTH_I32 || depth_type == GBX_DEPTH_I16, GBX_ERR_INVALID_VALUE, "depth_type");
+    for (int32_t k = 0; k < S; ++k)
+        GBX_CHECK(sources[k] >= 0 && sources[k] < G->n, GBX_ERR_INVALID_INDEX, "source outside [0, n)");
+    gbx_desc d;
+    if (desc)
+        d = *desc;
+    else
+        gbx_desc_init(&d);
+    GBX_CHECK(d.direction >= GBX_DIR_AUTO && d.direction <= GBX_DIR_PULL, GBX_ERR_INVALID_VALUE, "desc.direction");
+    GBX_CHECK(d.alpha >= 0.0f && d.alpha == d.alpha, GBX_ERR_INVALID_VALUE, "desc.alpha must be >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int32_t w_raw = (S + 63) / 64;
+    const int cw = w_raw >= 4 ? 4 : (w_raw >= 2 ? 2 : 1);
+    const int32_t W = (w_raw + cw - 1) / cw * cw;
+    GBX_TRY(ms_reserve(G, W, S, s));
+    // sources: pinned staging, then one async copy (the staging buffer is reused only
+    // after the previous copy has completed)
+    GBX_CUDA_TRY(cudaEventSynchronize(G->ms_src_ready));
+    for (int32_t k = 0; k < S; ++k) G->ms_src_pinned[k] = sources[k];
+    GBX_CUDA_TRY(cudaMemcpyAsync(G->ms_src, G->ms_src_pinned, sizeof(int32_t) * (size_t)S, cudaMemcpyHostToDevice, s));
+    GBX_CUDA_TRY(cudaEventRecord(G->ms_src_ready, s));
+    MsArgs a;
+    a.n = G->n;
+    a.S = S;
+    a.W = W;
+    a.nwords = G->nwords;
+    a.nnz = G->nnz;
+    a.out_ptr = G->out_ptr;
+    a.out_col = G->out_col;
+    a.in_ptr = G->in_ptr;
+    a.in_col = G->in_col;
+    a.nz_in = G->nz_in;
+    a.V = G->msV;
+    a.F = G->msF;
+    a.N = G->msN;
+    a.D = G->bm[2];
+    a.T = G->bm[3];
+    a.tlist = G->list;
+    a.depth = depth;
+    a.depth16 = depth_type == GBX_DEPTH_I16 ? 1 : 0;
+    a.src = G->ms_src;
+    for (int i = 0; i < 2; ++i) {
+        a.q[i] = G->q[i];
+        a.qp[i] = G->qp[i];
+        a.qd[i] = G->qd[i];
+    }
+    a.ctr = G->ctr;
+    a.bar = G->bar;
+    a.bar_parity = G->bar_parity;
+    a.trace = G->trace;
+    a.status = G->status;
+    a.alpha = d.alpha;
+    a.mode = d.direction;
+    a.symmetric = G->symmetric;
+    a.trace_cap = kTraceCap;
+    a.timeout_ns = wait_timeout_ns();
+    gbx_status st = cw == 4 ? ms_launch<4>(G, a, s) : (cw == 2 ? ms_launch<2>(G, a, s) : ms_launch<1>(G, a, s));
+    if (st != GBX_OK) return st;
+    G->bar_parity ^= 1u;
+    G->last_stream = s;
+    G->last_traced = 2;  // batched trace
+    return GBX_OK;
+}
+
+extern "C" gbx_status gbx_bfs_batch_trace(gbx_graph* g, gbx_level* levels, int32_t cap, int32_t* nlevels) {
+    clear_error();
+    GBX_TRY(check_graph(g));
+    Graph* G = as_impl(g);
+    GBX_CHECK(nlevels != nullptr, GBX_ERR_NULL_POINTER, "nlevels is NULL");
+    GBX_CHECK(cap == 0 || levels != nullptr, GBX_ERR_NULL_POINTER, "levels is NULL");
+    GBX_CHECK(G->last_traced == 2, GBX_ERR_INVALID_VALUE, "the last run on this graph was not a batched BFS");
+    if (G->last_stream) GBX_CUDA_TRY(cudaStreamSynchronize(G->last_stream));
+    int32_t st[ST_WORDS];
+    GBX_CUDA_TRY(cudaMemcpy(st, G->status, sizeof(st), cudaMemcpyDeviceToHost));
+    GBX_CHECK(st[ST_ERROR] == 0, (gbx_status)st[ST_ERROR], "the last batched BFS recorded a device-side error");
+    *nlevels = st[ST_LEVELS];
+    const int32_t L = st[ST_LEVELS] < kTraceCap ? st[ST_LEVELS] : kTraceCap;
+    const int32_t ncopy = L < cap ? L : cap;
+    if (ncopy <= 0) return GBX_OK;
+    LevelRec* recs = new LevelRec[ncopy];
+    const cudaError_t e = cudaMemcpy(recs, G->trace, sizeof(LevelRec) * ncopy, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        delete[] recs;
+        GBX_CUDA_TRY(e);
+    }
+    for (int32_t l = 0; l < ncopy; ++l) {
+        const LevelRec& r = recs[l];
+        gbx_level o = {};
+        o.direction = r.direction;
+        o.level = r.level;
+        o.nf = r.nf;          // active vertices (any lane)
+        o.mf = r.mf;          // their out-edges
+        o.nu = -1;
+        o.nu_nz = -1;
+        o.mu = r.mu;          // (vertex, lane) pairs found at the previous level
+        o.e_exam = r.e_exam;  // pull: edges examined (per 256-lane chunk)
+        o.n_new = r.n_new;    // (vertex, lane) pairs found at this level
+        o.mf_new = r.mf_new;  // out-edges of the next active list
+        o.time_ns = r.t_ns;
+        levels[l] = o;
+    }
+    delete[] recs;
+    return GBX_OK;
+}

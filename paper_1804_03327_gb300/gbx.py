@@ -43,12 +43,14 @@ DIR_PULL = 2
 HEUR_RATIO = 0
 HEUR_BEAMER = 1
 LOR_LAND = 0
+DEPTH_I32 = 0
+DEPTH_I16 = 1
 
 EXPORTED = [
     "gbx_last_error", "gbx_status_string", "gbx_version", "gbx_graph_build", "gbx_graph_free", "gbx_graph_info",
     "gbx_graph_csr", "gbx_graph_copy_csr", "gbx_graph_sync", "gbx_desc_init", "gbx_mxv", "gbx_mxv_stats",
     "gbx_bfs", "gbx_bfs_host", "gbx_bfs_trace", "gbx_set_wait_timeout_ns", "gbx_selftest_barrier_timeout",
-    "gbx_mxv_pull_noalloc",
+    "gbx_mxv_pull_noalloc", "gbx_bfs_batch", "gbx_bfs_batch_trace",
 ]
 
 
@@ -115,6 +117,8 @@ def load():
                 "gbx_set_wait_timeout_ns": (ctypes.c_int, [u64]),
                 "gbx_selftest_barrier_timeout": (ctypes.c_int, [p, u64, p]),
                 "gbx_mxv_pull_noalloc": (ctypes.c_int, [i32, p, p, p, p, i32, i32, p, p]),
+                "gbx_bfs_batch": (ctypes.c_int, [p, p, i32, p, i32, ctypes.POINTER(Desc), p]),
+                "gbx_bfs_batch_trace": (ctypes.c_int, [p, ctypes.POINTER(Level), i32, ctypes.POINTER(i32)]),
             }
             for name, (res, args) in sigs.items():
                 fn = getattr(L, name)
@@ -302,11 +306,28 @@ def bfs_host(g: Graph, sources, depth_host: np.ndarray, parent_host: np.ndarray 
     _check(st, "gbx_bfs_host")
 
 
+def bfs_batch(g: Graph, sources, depth, desc: Desc | None = None, stream=None):
+    """Multi-source BFS into a CUDA tensor depth[S, n] (int32 or int16)."""
+    srcs = np.ascontiguousarray(sources, dtype=np.int32)
+    dt = DEPTH_I16 if str(depth.dtype) == "torch.int16" else DEPTH_I32
+    _check(load().gbx_bfs_batch(g.handle, srcs.ctypes.data, len(srcs), depth.data_ptr(), dt,
+                                ctypes.byref(desc) if desc is not None else None, _stream_ptr(stream)),
+           "gbx_bfs_batch")
+
+
+def bfs_batch_trace(g: Graph, cap: int = 1 << 16) -> np.ndarray:
+    return _levels(g, cap, "gbx_bfs_batch_trace")
+
+
 def bfs_trace(g: Graph, cap: int = 1 << 16) -> np.ndarray:
     """Per-level records of the last traced BFS as a numpy structured array."""
+    return _levels(g, cap, "gbx_bfs_trace")
+
+
+def _levels(g: Graph, cap: int, fn: str) -> np.ndarray:
     buf = (Level * cap)()
     nl = ctypes.c_int32()
-    _check(load().gbx_bfs_trace(g.handle, buf, cap, ctypes.byref(nl)), "gbx_bfs_trace")
+    _check(getattr(load(), fn)(g.handle, buf, cap, ctypes.byref(nl)), fn)
     k = min(nl.value, cap)
     dt = np.dtype([(f, np.int64) for f in LEVEL_FIELDS])
     out = np.zeros(k, dtype=dt)
