@@ -301,6 +301,72 @@ gbx_status gbx_bfs_batch(gbx_graph* g, const int32_t* sources, int32_t S, void* 
  * chunk), n_new = pairs found at this level, mf_new, time_ns; nu and nu_nz are -1. */
 gbx_status gbx_bfs_batch_trace(gbx_graph* g, gbx_level* levels, int32_t cap, int32_t* nlevels);
 
+/* ------------------------------------------------------------------ server */
+
+/*
+ * Continuous-batching BFS server over several resident graphs (the batched
+ * form of Algorithm 1 applied to queries as they arrive; the paper runs one
+ * source at a time, this is the serving pattern built on gbx_bfs_batch).
+ * Queries queue per graph; whenever one of `slots` streams is free, the graph
+ * whose oldest query has waited longest sends up to its lane width of queued
+ * queries as one batched BFS, each lane writing its depths straight into the
+ * query's output row; each batch's persistent kernel gets 1/slots of the GPU so
+ * batches of different graphs run side by side.  A graph has one batch in
+ * flight at a time (its scratch is shared), and graphs added to a server must
+ * not be used by other calls while the server lives.
+ */
+typedef struct gbx_server gbx_server;
+
+typedef struct {
+    int32_t max_batch;     /* sources per batch, <= 4096 (default 64) */
+    int32_t slots;         /* batches in flight at once, 1..16 (default 2) */
+    int32_t depth_type;    /* GBX_DEPTH_I32 (default) or GBX_DEPTH_I16 output rows */
+    float alpha;           /* batch push -> pull threshold, as desc.alpha of gbx_bfs_batch (default 0.05) */
+    int64_t max_pending;   /* queued queries beyond which submit fails with GBX_ERR_BUSY (default 65536) */
+    int64_t memory_budget; /* device bytes of batch scratch all graphs may hold; 0 = unlimited.  A graph's
+                              lane width is the largest that fits (admission by memory). */
+    int32_t reserved[4];   /* must be 0 */
+} gbx_server_config;
+
+/* One finished query.  Times are host seconds since the server was created:
+ * submitted, its batch launched, its completion observed by submit/poll. */
+typedef struct {
+    uint64_t tag;
+    int32_t graph_id;
+    int32_t source;
+    int32_t status;     /* GBX_OK, or the device-side error of its batch */
+    int32_t levels;     /* levels of its batch (max over the batch's lanes) */
+    int32_t batch_size; /* queries in its batch */
+    int32_t reserved;
+    double t_submit;
+    double t_launch;
+    double t_done;
+} gbx_completion;
+
+void gbx_server_config_init(gbx_server_config* c);
+/* Create a server (allocates per-slot streams and staging).  Errors: NULL_POINTER,
+ * INVALID_VALUE (config), OUT_OF_MEMORY, CUDA. */
+gbx_status gbx_server_create(gbx_server** out, const gbx_server_config* cfg);
+/* Register a graph (not owned: free it after gbx_server_destroy); reserves its
+ * batch scratch within the memory budget.  Errors: OUT_OF_MEMORY when not even one
+ * lane fits, INVALID_VALUE if already added. */
+gbx_status gbx_server_add_graph(gbx_server* s, gbx_graph* g, int32_t* graph_id);
+/* Lane width (sources per batch) the server chose for a graph. */
+gbx_status gbx_server_graph_lanes(gbx_server* s, int32_t graph_id, int32_t* lanes);
+/* Queue a BFS from `source` on graph `graph_id`; its depths (n entries of the
+ * server's depth type, device memory, caller-owned, untouched until the query
+ * completes) go to depth_out.  May start batches.  Errors: BUSY (queue full),
+ * INVALID_INDEX, NULL_POINTER. */
+gbx_status gbx_server_submit(gbx_server* s, int32_t graph_id, int32_t source, void* depth_out, uint64_t tag);
+/* Collect finished batches, start new ones on free slots, and return up to max
+ * completions (oldest first) in out; *nout receives how many. */
+gbx_status gbx_server_poll(gbx_server* s, gbx_completion* out, int32_t max, int32_t* nout);
+/* Queued queries, queries in flight, submissions refused, scratch bytes held. */
+gbx_status gbx_server_stats(gbx_server* s, int64_t* queued, int32_t* in_flight, int64_t* rejected,
+                            int64_t* scratch_bytes);
+/* Wait for batches in flight and release the server (not the graphs). */
+gbx_status gbx_server_destroy(gbx_server* s);
+
 /* Upper bound, in nanoseconds, of every device-side wait in this library (the
  * persistent kernels' grid barriers).  When it runs out the kernel records
  * GBX_ERR_TIMEOUT and returns.  Default 5e9.  Process-wide. */

@@ -255,4 +255,10 @@ inline const Graph* as_impl(const gbx_graph* g) { return reinterpret_cast<const 
 
 gbx_status graph_scratch_alloc(Graph* g);
 
+// Batched BFS internals (msbfs.cu), shared with the server.
+gbx_status ms_reserve(Graph* G, int32_t S, cudaStream_t s);
+int64_t ms_scratch_bytes(int32_t n, int32_t S);
+gbx_status ms_run(Graph* G, int32_t S, const int32_t* src_dev, void* depth, void* const* rows, int depth16,
+                  const gbx_desc& d, int blocks, cudaStream_t s);
+
 }  // namespace gbx

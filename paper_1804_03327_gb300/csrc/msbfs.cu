@@ -40,7 +40,8 @@ struct MsArgs {
     uint32_t* D;        // all lanes visited
     uint32_t* T;        // touched by the current push level
     int32_t* tlist;     // touched vertices
-    void* depth;        // [S][n]
+    void* depth;        // [S][n], used when rows is NULL
+    void* const* rows;  // optional: lane b writes its n depths to rows[b]
     int depth16;
     const int32_t* src;
     int32_t* q[2];
@@ -64,6 +65,13 @@ __device__ __forceinline__ unsigned long long lane_mask(int32_t S, int32_t w) {
 }
 
 __device__ __forceinline__ void store_depth(const MsArgs& a, int32_t lane_b, int32_t v, int32_t d) {
+    if (a.rows) {
+        if (a.depth16)
+            static_cast<int16_t*>(a.rows[lane_b])[v] = (int16_t)d;
+        else
+            static_cast<int32_t*>(a.rows[lane_b])[v] = d;
+        return;
+    }
     const size_t idx = (size_t)lane_b * (size_t)a.n + (size_t)v;
     if (a.depth16)
         static_cast<int16_t*>(a.depth)[idx] = (int16_t)d;
@@ -339,7 +347,15 @@ __global__ void __launch_bounds__(kMsThreads, 1) ms_bfs_kernel(MsArgs a) {
         a.T[w] = 0u;
     }
     const size_t nd = (size_t)a.S * (size_t)a.n;
-    if (a.depth16) {
+    if (a.rows) {
+        for (size_t i = gtid; i < nd; i += gstride) {
+            const size_t b = i / (size_t)a.n, v = i - b * (size_t)a.n;
+            if (a.depth16)
+                static_cast<int16_t*>(a.rows[b])[v] = (int16_t)-1;
+            else
+                static_cast<int32_t*>(a.rows[b])[v] = -1;
+        }
+    } else if (a.depth16) {
         int16_t* d = static_cast<int16_t*>(a.depth);
         for (size_t i = gtid; i < nd; i += gstride) d[i] = (int16_t)-1;
     } else {
@@ -473,8 +489,10 @@ __global__ void __launch_bounds__(kMsThreads, 1) ms_bfs_kernel(MsArgs a) {
     }
 }
 
-static gbx_status ms_reserve(Graph* G, int32_t W, int32_t S, cudaStream_t s) {
-    const int64_t need = (int64_t)G->n * W;
+gbx_status ms_reserve(Graph* G, int32_t S, cudaStream_t s) {
+    const int32_t w_raw = (S + 63) / 64;
+    const int cw = w_raw >= 4 ? 4 : (w_raw >= 2 ? 2 : 1);
+    const int64_t need = (int64_t)G->n * ((w_raw + cw - 1) / cw * cw);
     if (G->ms_cap_words < need) {
         if (G->msV) {
             GBX_CUDA_TRY(cudaStreamSynchronize(s));
@@ -489,31 +507,80 @@ static gbx_status ms_reserve(Graph* G, int32_t W, int32_t S, cudaStream_t s) {
         GBX_CUDA_TRY(cudaMalloc((void**)&G->msN, sizeof(unsigned long long) * (size_t)need));
         G->ms_cap_words = need;
     }
-    if (G->ms_src_cap < S) {
-        if (G->ms_src) {
-            GBX_CUDA_TRY(cudaStreamSynchronize(s));
-            cudaFree(G->ms_src);
-            cudaFreeHost(G->ms_src_pinned);
-            G->ms_src = nullptr;
-            G->ms_src_pinned = nullptr;
-        }
-        GBX_CUDA_TRY(cudaMalloc((void**)&G->ms_src, sizeof(int32_t) * (size_t)S));
-        GBX_CUDA_TRY(cudaMallocHost((void**)&G->ms_src_pinned, sizeof(int32_t) * (size_t)S));
-        G->ms_src_cap = S;
-    }
-    if (!G->ms_src_ready) GBX_CUDA_TRY(cudaEventCreateWithFlags(&G->ms_src_ready, cudaEventDisableTiming));
     return GBX_OK;
 }
 
+int64_t ms_scratch_bytes(int32_t n, int32_t S) {
+    const int32_t w_raw = (S + 63) / 64;
+    const int cw = w_raw >= 4 ? 4 : (w_raw >= 2 ? 2 : 1);
+    return 3ll * 8ll * (int64_t)n * ((w_raw + cw - 1) / cw * cw);
+}
+
 template <int CW>
-static gbx_status ms_launch(Graph* G, const MsArgs& a0, cudaStream_t s) {
+static gbx_status ms_launch(Graph* G, const MsArgs& a0, int blocks, cudaStream_t s) {
     int per_sm = 0;
     GBX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ms_bfs_kernel<CW>, kMsThreads, 0));
     GBX_CHECK(per_sm >= 1, GBX_ERR_CUDA, "batched BFS kernel cannot be resident");
+    const int full = per_sm * G->num_sms;
+    const int nb = blocks > 1 ? (full / blocks > 0 ? full / blocks : 1) : full;  // a 1/blocks share of the GPU
     MsArgs a = a0;
     void* args[] = {&a};
-    GBX_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)ms_bfs_kernel<CW>, dim3(per_sm * G->num_sms),
-                                             dim3(kMsThreads), args, 0, s));
+    GBX_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)ms_bfs_kernel<CW>, dim3(nb), dim3(kMsThreads), args, 0, s));
+    return GBX_OK;
+}
+
+// One batched BFS on G: sources already on the device (src_dev), depth either a
+// [S][n] buffer or a device table of S row pointers.  `blocks` > 1 runs the
+// persistent kernel on 1/blocks of the GPU's resident blocks (so that many
+// batches of other graphs fit alongside); scratch must be reserved for S lanes.
+gbx_status ms_run(Graph* G, int32_t S, const int32_t* src_dev, void* depth, void* const* rows, int depth16,
+                  const gbx_desc& d, int blocks, cudaStream_t s) {
+    const int32_t w_raw = (S + 63) / 64;
+    const int cw = w_raw >= 4 ? 4 : (w_raw >= 2 ? 2 : 1);
+    const int32_t W = (w_raw + cw - 1) / cw * cw;
+    GBX_CHECK(G->ms_cap_words >= (int64_t)G->n * W, GBX_ERR_INVALID_VALUE, "batch scratch not reserved");
+    MsArgs a;
+    a.n = G->n;
+    a.S = S;
+    a.W = W;
+    a.nwords = G->nwords;
+    a.nnz = G->nnz;
+    a.out_ptr = G->out_ptr;
+    a.out_col = G->out_col;
+    a.in_ptr = G->in_ptr;
+    a.in_col = G->in_col;
+    a.nz_in = G->nz_in;
+    a.V = G->msV;
+    a.F = G->msF;
+    a.N = G->msN;
+    a.D = G->bm[2];
+    a.T = G->bm[3];
+    a.tlist = G->list;
+    a.depth = depth;
+    a.rows = rows;
+    a.depth16 = depth16;
+    a.src = src_dev;
+    for (int i = 0; i < 2; ++i) {
+        a.q[i] = G->q[i];
+        a.qp[i] = G->qp[i];
+        a.qd[i] = G->qd[i];
+    }
+    a.ctr = G->ctr;
+    a.bar = G->bar;
+    a.bar_parity = G->bar_parity;
+    a.trace = G->trace;
+    a.status = G->status;
+    a.alpha = d.alpha;
+    a.mode = d.direction;
+    a.symmetric = G->symmetric;
+    a.trace_cap = kTraceCap;
+    a.timeout_ns = wait_timeout_ns();
+    const gbx_status st = cw == 4 ? ms_launch<4>(G, a, blocks, s)
+                                  : (cw == 2 ? ms_launch<2>(G, a, blocks, s) : ms_launch<1>(G, a, blocks, s));
+    if (st != GBX_OK) return st;
+    G->bar_parity ^= 1u;
+    G->last_stream = s;
+    G->last_traced = 2;  // batched trace
     return GBX_OK;
 }
 
@@ -539,57 +606,27 @@ extern "C" gbx_status gbx_bfs_batch(gbx_graph* g, const int32_t* sources, int32_
     GBX_CHECK(d.direction >= GBX_DIR_AUTO && d.direction <= GBX_DIR_PULL, GBX_ERR_INVALID_VALUE, "desc.direction");
     GBX_CHECK(d.alpha >= 0.0f && d.alpha == d.alpha, GBX_ERR_INVALID_VALUE, "desc.alpha must be >= 0");
     cudaStream_t s = (cudaStream_t)stream;
-    const int32_t w_raw = (S + 63) / 64;
-    const int cw = w_raw >= 4 ? 4 : (w_raw >= 2 ? 2 : 1);
-    const int32_t W = (w_raw + cw - 1) / cw * cw;
-    GBX_TRY(ms_reserve(G, W, S, s));
+    GBX_TRY(ms_reserve(G, S, s));
+    if (G->ms_src_cap < S) {
+        if (G->ms_src) {
+            GBX_CUDA_TRY(cudaStreamSynchronize(s));
+            cudaFree(G->ms_src);
+            cudaFreeHost(G->ms_src_pinned);
+            G->ms_src = nullptr;
+            G->ms_src_pinned = nullptr;
+        }
+        GBX_CUDA_TRY(cudaMalloc((void**)&G->ms_src, sizeof(int32_t) * (size_t)S));
+        GBX_CUDA_TRY(cudaMallocHost((void**)&G->ms_src_pinned, sizeof(int32_t) * (size_t)S));
+        G->ms_src_cap = S;
+    }
+    if (!G->ms_src_ready) GBX_CUDA_TRY(cudaEventCreateWithFlags(&G->ms_src_ready, cudaEventDisableTiming));
     // sources: pinned staging, then one async copy (the staging buffer is reused only
     // after the previous copy has completed)
     GBX_CUDA_TRY(cudaEventSynchronize(G->ms_src_ready));
     for (int32_t k = 0; k < S; ++k) G->ms_src_pinned[k] = sources[k];
     GBX_CUDA_TRY(cudaMemcpyAsync(G->ms_src, G->ms_src_pinned, sizeof(int32_t) * (size_t)S, cudaMemcpyHostToDevice, s));
     GBX_CUDA_TRY(cudaEventRecord(G->ms_src_ready, s));
-    MsArgs a;
-    a.n = G->n;
-    a.S = S;
-    a.W = W;
-    a.nwords = G->nwords;
-    a.nnz = G->nnz;
-    a.out_ptr = G->out_ptr;
-    a.out_col = G->out_col;
-    a.in_ptr = G->in_ptr;
-    a.in_col = G->in_col;
-    a.nz_in = G->nz_in;
-    a.V = G->msV;
-    a.F = G->msF;
-    a.N = G->msN;
-    a.D = G->bm[2];
-    a.T = G->bm[3];
-    a.tlist = G->list;
-    a.depth = depth;
-    a.depth16 = depth_type == GBX_DEPTH_I16 ? 1 : 0;
-    a.src = G->ms_src;
-    for (int i = 0; i < 2; ++i) {
-        a.q[i] = G->q[i];
-        a.qp[i] = G->qp[i];
-        a.qd[i] = G->qd[i];
-    }
-    a.ctr = G->ctr;
-    a.bar = G->bar;
-    a.bar_parity = G->bar_parity;
-    a.trace = G->trace;
-    a.status = G->status;
-    a.alpha = d.alpha;
-    a.mode = d.direction;
-    a.symmetric = G->symmetric;
-    a.trace_cap = kTraceCap;
-    a.timeout_ns = wait_timeout_ns();
-    gbx_status st = cw == 4 ? ms_launch<4>(G, a, s) : (cw == 2 ? ms_launch<2>(G, a, s) : ms_launch<1>(G, a, s));
-    if (st != GBX_OK) return st;
-    G->bar_parity ^= 1u;
-    G->last_stream = s;
-    G->last_traced = 2;  // batched trace
-    return GBX_OK;
+    return ms_run(G, S, G->ms_src, depth, nullptr, depth_type == GBX_DEPTH_I16 ? 1 : 0, d, 0, s);
 }
 
 extern "C" gbx_status gbx_bfs_batch_trace(gbx_graph* g, gbx_level* levels, int32_t cap, int32_t* nlevels) {

@@ -51,6 +51,8 @@ EXPORTED = [
     "gbx_graph_csr", "gbx_graph_copy_csr", "gbx_graph_sync", "gbx_desc_init", "gbx_mxv", "gbx_mxv_stats",
     "gbx_bfs", "gbx_bfs_host", "gbx_bfs_trace", "gbx_set_wait_timeout_ns", "gbx_selftest_barrier_timeout",
     "gbx_mxv_pull_noalloc", "gbx_bfs_batch", "gbx_bfs_batch_trace",
+    "gbx_server_config_init", "gbx_server_create", "gbx_server_add_graph", "gbx_server_graph_lanes",
+    "gbx_server_submit", "gbx_server_poll", "gbx_server_stats", "gbx_server_destroy",
 ]
 
 
@@ -77,6 +79,19 @@ class Level(ctypes.Structure):
                 ("mf", ctypes.c_int64), ("nu", ctypes.c_int64), ("nu_nz", ctypes.c_int64), ("mu", ctypes.c_int64),
                 ("e_exam", ctypes.c_int64), ("n_new", ctypes.c_int64), ("mf_new", ctypes.c_int64),
                 ("time_ns", ctypes.c_int64)]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("max_batch", ctypes.c_int32), ("slots", ctypes.c_int32), ("depth_type", ctypes.c_int32),
+                ("alpha", ctypes.c_float), ("max_pending", ctypes.c_int64), ("memory_budget", ctypes.c_int64),
+                ("reserved", ctypes.c_int32 * 4)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("graph_id", ctypes.c_int32), ("source", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("levels", ctypes.c_int32), ("batch_size", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("t_submit", ctypes.c_double), ("t_launch", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
 
 
 LEVEL_FIELDS = ["direction", "level", "nf", "mf", "nu", "nu_nz", "mu", "e_exam", "n_new", "mf_new", "time_ns"]
@@ -119,6 +134,15 @@ def load():
                 "gbx_mxv_pull_noalloc": (ctypes.c_int, [i32, p, p, p, p, i32, i32, p, p]),
                 "gbx_bfs_batch": (ctypes.c_int, [p, p, i32, p, i32, ctypes.POINTER(Desc), p]),
                 "gbx_bfs_batch_trace": (ctypes.c_int, [p, ctypes.POINTER(Level), i32, ctypes.POINTER(i32)]),
+                "gbx_server_config_init": (None, [ctypes.POINTER(ServerConfig)]),
+                "gbx_server_create": (ctypes.c_int, [ctypes.POINTER(p), ctypes.POINTER(ServerConfig)]),
+                "gbx_server_add_graph": (ctypes.c_int, [p, p, ctypes.POINTER(i32)]),
+                "gbx_server_graph_lanes": (ctypes.c_int, [p, i32, ctypes.POINTER(i32)]),
+                "gbx_server_submit": (ctypes.c_int, [p, i32, i32, p, u64]),
+                "gbx_server_poll": (ctypes.c_int, [p, ctypes.POINTER(Completion), i32, ctypes.POINTER(i32)]),
+                "gbx_server_stats": (ctypes.c_int, [p, ctypes.POINTER(i64), ctypes.POINTER(i32),
+                                                    ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+                "gbx_server_destroy": (ctypes.c_int, [p]),
             }
             for name, (res, args) in sigs.items():
                 fn = getattr(L, name)
@@ -335,3 +359,57 @@ def _levels(g: Graph, cap: int, fn: str) -> np.ndarray:
         for f in LEVEL_FIELDS:
             out[i][f] = getattr(buf[i], f)
     return out
+
+
+class Server:
+    """Continuous-batching BFS server (gbx_server_*)."""
+
+    def __init__(self, **cfg):
+        c = ServerConfig()
+        load().gbx_server_config_init(ctypes.byref(c))
+        for k, v in cfg.items():
+            setattr(c, k, v)
+        h = ctypes.c_void_p()
+        _check(load().gbx_server_create(ctypes.byref(h), ctypes.byref(c)), "gbx_server_create")
+        self._h = h.value
+        self._buf = (Completion * 4096)()
+
+    def add_graph(self, g: Graph) -> int:
+        gid = ctypes.c_int32()
+        _check(load().gbx_server_add_graph(self._h, g.handle, ctypes.byref(gid)), "gbx_server_add_graph")
+        return gid.value
+
+    def lanes(self, gid: int) -> int:
+        x = ctypes.c_int32()
+        _check(load().gbx_server_graph_lanes(self._h, gid, ctypes.byref(x)), "gbx_server_graph_lanes")
+        return x.value
+
+    def submit(self, gid: int, source: int, out, tag: int) -> bool:
+        """Queue a query; False if the server refused it (queue full)."""
+        st = load().gbx_server_submit(self._h, int(gid), int(source), out.data_ptr(), int(tag))
+        if st == ERR_BUSY:
+            return False
+        _check(st, "gbx_server_submit")
+        return True
+
+    def poll(self) -> list:
+        n = ctypes.c_int32()
+        _check(load().gbx_server_poll(self._h, self._buf, len(self._buf), ctypes.byref(n)), "gbx_server_poll")
+        return [self._buf[i] for i in range(n.value)]
+
+    def stats(self) -> dict:
+        q, f, r, b = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+        _check(load().gbx_server_stats(self._h, ctypes.byref(q), ctypes.byref(f), ctypes.byref(r), ctypes.byref(b)),
+               "gbx_server_stats")
+        return {"queued": q.value, "in_flight": f.value, "rejected": r.value, "scratch_bytes": b.value}
+
+    def destroy(self):
+        if self._h:
+            _check(load().gbx_server_destroy(self._h), "gbx_server_destroy")
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass

@@ -106,3 +106,17 @@ def test_byte_model_on_oracle_trace():
     want = 8 * n + sum(12 * r["nf"] + 4 * r["mf"] + 12 * r["n_new"] + bm for r in tr)
     assert roofline.bfs_bytes(rec, n) == want
     assert roofline.reached_edges(rec) == k  # star: k undirected edges, all reached
+
+
+def test_server_config_validation_on_host(lib):
+    c = gbx.ServerConfig()
+    lib.gbx_server_config_init(ctypes.byref(c))
+    assert (c.max_batch, c.slots, c.depth_type, c.max_pending, c.memory_budget) == (64, 2, 0, 1 << 16, 0)
+    h = ctypes.c_void_p()
+    for field, bad in [("max_batch", 0), ("slots", 17), ("depth_type", 5), ("max_pending", 0), ("memory_budget", -1)]:
+        c2 = gbx.ServerConfig()
+        lib.gbx_server_config_init(ctypes.byref(c2))
+        setattr(c2, field, bad)
+        assert lib.gbx_server_create(ctypes.byref(h), ctypes.byref(c2)) == gbx.ERR_INVALID_VALUE, field
+    assert lib.gbx_server_submit(None, 0, 0, None, 0) == gbx.ERR_NULL_POINTER
+    assert lib.gbx_server_destroy(None) == gbx.OK
