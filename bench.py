@@ -53,6 +53,10 @@ def parse():
     p.add_argument("--scale", type=int, default=SCALE)
     p.add_argument("--cpu-sample", type=int, default=8, help="sources the CPU oracle baseline times")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-batched", action="store_true", help="skip the batched multi-source measurements")
+    p.add_argument("--no-served", action="store_true", help="skip the serving measurement")
+    p.add_argument("--serve-seconds", type=float, default=2.0)
+    p.add_argument("--serve-rate", type=float, default=20000.0)
     p.add_argument("--probe", type=int, default=None, metavar="K",
                    help="profiling aid: run only source K of the workload --repeat times (for ncu -k bfs_kernel)")
     p.add_argument("--repeat", type=int, default=5)
@@ -247,6 +251,166 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def batched_measurements(g, n, sources, reached, single_value, args):
+    """Batched multi-source BFS: the benchmark's own sources as one batch on the
+    same graph, then RMAT scale 21 and the 2048x2048 grid at several widths."""
+    import torch
+
+    import synth
+    from paper_1804_03327_gb300 import gbx
+
+    def time_batch(gg, srcs, nn, reps=3):
+        depth = torch.empty((len(srcs), nn), dtype=torch.int16, device="cuda")
+        gbx.bfs_batch(gg, srcs, depth)
+        gbx.graph_sync(gg)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            gbx.bfs_batch(gg, srcs, depth)
+        e1.record()
+        torch.cuda.synchronize()
+        gbx.graph_sync(gg)
+        del depth
+        return e0.elapsed_time(e1) / reps / 1e3
+
+    def reached_of(gg, srcs, nn):
+        # reached undirected edges per source, from one traced single-source BFS each
+        from paper_1804_03327_gb300 import roofline
+        d = torch.empty(nn, dtype=torch.int32, device="cuda")
+        out = []
+        for s0 in srcs:
+            gbx.bfs(gg, int(s0), d, None, gbx.desc_init(trace=1))
+            out.append(roofline.reached_edges(gbx.bfs_trace(gg)))
+        return out
+
+    res = {}
+    t = time_batch(g, sources, n)
+    v = sum(reached) / t / 1e9
+    res["same_sources_as_one_batch"] = {"workload": WORKLOAD, "S": len(sources), "ms": t * 1e3, "value": v,
+                                        "unit": UNIT, "vs_single_source": v / single_value}
+    cfg4 = []
+    for name, gen in [("rmat21-ef16", lambda: synth.rmat_edges(21, EDGE_FACTOR, seed=SEED)),
+                      ("grid2048-del1pct", lambda: synth.grid_edges(2048, 2048, 0.01, seed=SEED))]:
+        nn, ss, dd = gen()
+        gg = gbx.graph_build(nn, ss, dd)
+        widths = (64, 256, 1024) if name.startswith("rmat") else (64,)
+        all_src = synth.sources(nn, ss, dd, max(widths), seed=SEED)
+        # single-source reference on the first 64 of these sources
+        d = torch.empty(nn, dtype=torch.int32, device="cuda")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        gbx.bfs(gg, int(all_src[0]), d, None)
+        e0.record()
+        for s0 in all_src[:64]:
+            gbx.bfs(gg, int(s0), d, None)
+        e1.record()
+        torch.cuda.synchronize()
+        single_s = e0.elapsed_time(e1) / 1e3 / 64
+        reach = reached_of(gg, all_src, nn)
+        for S in widths:
+            tb = time_batch(gg, all_src[:S], nn, reps=1 if name.startswith("grid") else 3)
+            edges = sum(reach[:S])
+            cfg4.append({"graph": name, "S": S, "ms": tb * 1e3, "value": edges / tb / 1e9, "unit": UNIT,
+                         "single_source_value": edges / (single_s * S) / 1e9,
+                         "speedup_vs_single_source": single_s * S / tb})
+        gg.free()
+    res["configs"] = cfg4
+    return res
+
+
+def served_measurement(main_graph, args):
+    """Poisson arrivals of single-source queries over six resident graphs,
+    continuously batched by gbx_server; p50/p99 latency and GTEPS."""
+    import torch
+
+    import synth
+    from paper_1804_03327_gb300 import gbx, roofline
+
+    specs = [("rmat16", lambda: synth.rmat_edges(16, EDGE_FACTOR, seed=SEED)),
+             ("rmat18", lambda: synth.rmat_edges(18, EDGE_FACTOR, seed=SEED)),
+             ("rmat20", lambda: synth.rmat_edges(20, EDGE_FACTOR, seed=SEED)),
+             ("rmat22", None),
+             ("grid1024", lambda: synth.grid_edges(1024, 1024, 0.01, seed=SEED)),
+             ("grid2048", lambda: synth.grid_edges(2048, 2048, 0.01, seed=SEED))]
+    graphs = []
+    for name, gen in specs:
+        if gen is None:
+            g, n, src, dst = main_graph
+        else:
+            n, src, dst = gen()
+            g = gbx.graph_build(n, src, dst)
+        cand = synth.sources(n, src, dst, 256, seed=SEED + 7)
+        # reached edges of each candidate source (one traced BFS per connected component seen)
+        d = torch.empty(n, dtype=torch.int32, device="cuda")
+        reach = {}
+        for s0 in cand:
+            if int(s0) in reach:
+                continue
+            gbx.bfs(g, int(s0), d, None, gbx.desc_init(trace=1))
+            e = roofline.reached_edges(gbx.bfs_trace(g))
+            dn = d.cpu().numpy()
+            for s1 in cand:
+                if dn[int(s1)] >= 0:
+                    reach[int(s1)] = e
+        graphs.append({"name": name, "g": g, "n": n, "cand": cand, "reach": reach, "own": gen is not None})
+    srv = gbx.Server(max_batch=64, slots=4, depth_type=gbx.DEPTH_I16, max_pending=1 << 16)
+    for gi in graphs:
+        gi["id"] = srv.add_graph(gi["g"])
+        rows = 2048
+        gi["pool"] = torch.empty((rows, gi["n"]), dtype=torch.int16, device="cuda")
+        gi["free"] = list(range(rows))
+    rng = np.random.default_rng(SEED)
+    warm, span = 0.5, args.serve_seconds
+    t_arr = np.cumsum(rng.exponential(1.0 / args.serve_rate, size=int(args.serve_rate * (warm + span) * 1.2)))
+    t_arr = t_arr[t_arr < warm + span]
+    which = rng.integers(0, len(graphs), size=len(t_arr))
+    pick = rng.integers(0, 256, size=len(t_arr))
+    inflight = {}
+    lat, edges_done, refused, waited = [], 0, 0, 0
+    t0 = time.perf_counter()
+    i = 0
+    done_n = 0
+    while i < len(t_arr) or inflight:
+        now = time.perf_counter() - t0
+        while i < len(t_arr) and t_arr[i] <= now:
+            gi = graphs[which[i]]
+            if not gi["free"]:
+                waited += 1
+                break  # client has no free output row for this graph: wait for completions
+            slot = gi["free"].pop()
+            s0 = int(gi["cand"][pick[i]])
+            if srv.submit(gi["id"], s0, gi["pool"][slot], tag=i):
+                inflight[i] = (gi, slot, s0)
+            else:
+                gi["free"].append(slot)
+                refused += 1
+            i += 1
+        cs = srv.poll()
+        t_seen = time.perf_counter() - t0
+        for c in cs:
+            gi, slot, s0 = inflight.pop(c.tag)
+            gi["free"].append(slot)
+            done_n += 1
+            if t_arr[c.tag] >= warm:
+                lat.append(t_seen - t_arr[c.tag])  # arrival (scheduled) -> completion seen
+                edges_done += gi["reach"].get(s0, 0)
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.destroy()
+    for gi in graphs:
+        if gi["own"]:
+            gi["g"].free()
+    lat = np.array(lat) if lat else np.array([0.0])
+    measured_window = wall - warm
+    return {"graphs": [gi["name"] for gi in graphs], "arrival_rate_qps": args.serve_rate,
+            "arrivals": int(len(t_arr)), "measured_queries": int(len(lat)), "completed": done_n,
+            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "value": edges_done / measured_window / 1e9, "unit": UNIT,
+            "throughput_qps": len(lat) / measured_window, "refused": refused, "client_waits": waited,
+            "server": {"slots": 4, "max_batch": 64, "depth": "int16", "scratch_bytes": st["scratch_bytes"]},
+            "note": "latency = scheduled arrival -> completion observed by the client's poll; GTEPS and "
+                    "throughput over queries arriving after the 0.5 s warm-up"}
+
+
 def run_ours(args):
     import torch
 
@@ -349,6 +513,13 @@ def run_ours(args):
                "h2d_bytes_per_step": 4 * S, "d2h_bytes_per_step": 2 * 4 * n * S,
                "steps": e_steps, "api": "gbx_bfs_host (pinned host depth+parent, D2H overlapped with the next BFS)"}
 
+    batched = None
+    if rank == 0 and not args.no_batched:
+        batched = batched_measurements(g, n, sources, reached, value / world, args)
+    served = None
+    if rank == 0 and not args.no_served:
+        served = served_measurement((g, n, src, dst), args)
+
     cpu = None
     if rank == 0:
         v, dt, e = cpu_oracle_baseline(n, src, dst, sources, args.cpu_sample)
@@ -381,6 +552,8 @@ def run_ours(args):
         "per_source_gteps": {"hmean": float(len(per_src_gteps) / np.sum(1.0 / np.array(per_src_gteps))),
                              "median": float(np.median(per_src_gteps))},
         "schedule_example": dirs[0],
+        "batched": batched,
+        "served": served,
     }
     print(json.dumps(line), flush=True)
     g.free()
