@@ -310,10 +310,9 @@ gbx_status gbx_bfs_batch_trace(gbx_graph* g, gbx_level* levels, int32_t cap, int
  * Queries queue per graph; whenever one of `slots` streams is free, the graph
  * whose oldest query has waited longest sends up to its lane width of queued
  * queries as one batched BFS, each lane writing its depths straight into the
- * query's output row; each batch's persistent kernel gets 1/slots of the GPU so
- * batches of different graphs run side by side.  A graph has one batch in
- * flight at a time (its scratch is shared), and graphs added to a server must
- * not be used by other calls while the server lives.
+ * query's output row; each slot has its own scratch and its batch's persistent
+ * kernel gets 1/slots of the GPU, so batches -- of different graphs or of the
+ * same graph -- run side by side.  The graphs are only read by the server.
  */
 typedef struct gbx_server gbx_server;
 
@@ -323,8 +322,9 @@ typedef struct {
     int32_t depth_type;    /* GBX_DEPTH_I32 (default) or GBX_DEPTH_I16 output rows */
     float alpha;           /* batch push -> pull threshold, as desc.alpha of gbx_bfs_batch (default 0.05) */
     int64_t max_pending;   /* queued queries beyond which submit fails with GBX_ERR_BUSY (default 65536) */
-    int64_t memory_budget; /* device bytes of batch scratch all graphs may hold; 0 = unlimited.  A graph's
-                              lane width is the largest that fits (admission by memory). */
+    int64_t memory_budget; /* device bytes of batch scratch the slots may hold (each slot keeps scratch for
+                              the widest batch of any graph); 0 = unlimited.  A graph's lane width is the
+                              largest that fits (admission by memory). */
     int32_t reserved[4];   /* must be 0 */
 } gbx_server_config;
 

@@ -550,18 +550,18 @@ static gbx_status launch_bfs(Graph* G, int32_t source, int32_t* depth, int32_t* 
     a.first_in = G->first_in;
     a.depth = depth;
     a.parent = parent;
-    a.vis[0] = G->bm[0];
-    a.vis[1] = G->bm[1];
-    a.fbm = G->bm[2];
+    a.vis[0] = G->ws.bm[0];
+    a.vis[1] = G->ws.bm[1];
+    a.fbm = G->ws.bm[2];
     for (int i = 0; i < 2; ++i) {
-        a.q[i] = G->q[i];
-        a.qp[i] = G->qp[i];
-        a.qd[i] = G->qd[i];
+        a.q[i] = G->ws.q[i];
+        a.qp[i] = G->ws.qp[i];
+        a.qd[i] = G->ws.qd[i];
     }
-    a.ctr = G->ctr;
-    a.bar = G->bar;
-    a.trace = G->trace;
-    a.status = G->status;
+    a.ctr = G->ws.ctr;
+    a.bar = G->ws.bar;
+    a.trace = G->ws.trace;
+    a.status = G->ws.status;
     a.alpha = d.alpha;
     a.beta = d.beta;
     a.heuristic = d.heuristic;
@@ -573,13 +573,13 @@ static gbx_status launch_bfs(Graph* G, int32_t source, int32_t* depth, int32_t* 
     a.need_indeg = (!G->symmetric && (d.trace || d.heuristic == GBX_HEUR_BEAMER)) ? 1 : 0;
     a.trace_cap = kTraceCap;
     a.timeout_ns = wait_timeout_ns();
-    a.bar_parity = G->bar_parity;
+    a.bar_parity = G->ws.bar_parity;
     void* args[] = {&a};
     const void* fn = d.trace ? (const void*)bfs_kernel<true> : (const void*)bfs_kernel<false>;
     GBX_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(G->bfs_blocks), dim3(kBfsThreads), args, 0, s));
-    G->bar_parity ^= 1u;
-    G->last_stream = s;
-    G->last_traced = d.trace ? 1 : 0;
+    G->ws.bar_parity ^= 1u;
+    G->ws.last_stream = s;
+    G->ws.last_traced = d.trace ? 1 : 0;
     return GBX_OK;
 }
 
@@ -601,11 +601,11 @@ extern "C" gbx_status gbx_selftest_barrier_timeout(gbx_graph* g, uint64_t timeou
     clear_error();
     GBX_TRY(check_graph(g));
     Graph* G = as_impl(g);
-    selftest_barrier_kernel<<<4, 32, 0, (cudaStream_t)stream>>>(G->bar, G->bar_parity, G->status,
+    selftest_barrier_kernel<<<4, 32, 0, (cudaStream_t)stream>>>(G->ws.bar, G->ws.bar_parity, G->ws.status,
                                                                  (unsigned long long)timeout_ns);
-    G->bar_parity ^= 1u;
+    G->ws.bar_parity ^= 1u;
     GBX_CUDA_TRY(cudaGetLastError());
-    G->last_stream = (cudaStream_t)stream;
+    G->ws.last_stream = (cudaStream_t)stream;
     return GBX_OK;
 }
 
@@ -682,18 +682,18 @@ extern "C" gbx_status gbx_bfs_trace(gbx_graph* g, gbx_level* levels, int32_t cap
     Graph* G = as_impl(g);
     GBX_CHECK(nlevels != nullptr, GBX_ERR_NULL_POINTER, "nlevels is NULL");
     GBX_CHECK(cap == 0 || levels != nullptr, GBX_ERR_NULL_POINTER, "levels is NULL");
-    GBX_CHECK(G->last_traced, GBX_ERR_INVALID_VALUE, "the last BFS on this graph was not traced");
-    if (G->last_stream) GBX_CUDA_TRY(cudaStreamSynchronize(G->last_stream));
+    GBX_CHECK(G->ws.last_traced, GBX_ERR_INVALID_VALUE, "the last BFS on this graph was not traced");
+    if (G->ws.last_stream) GBX_CUDA_TRY(cudaStreamSynchronize(G->ws.last_stream));
     GBX_CUDA_TRY(cudaDeviceSynchronize());
     int32_t st[ST_WORDS];
-    GBX_CUDA_TRY(cudaMemcpy(st, G->status, sizeof(st), cudaMemcpyDeviceToHost));
+    GBX_CUDA_TRY(cudaMemcpy(st, G->ws.status, sizeof(st), cudaMemcpyDeviceToHost));
     GBX_CHECK(st[ST_ERROR] == 0, (gbx_status)st[ST_ERROR], "the last BFS recorded a device-side error");
     const int32_t L = st[ST_LEVELS] < kTraceCap ? st[ST_LEVELS] : kTraceCap;
     *nlevels = st[ST_LEVELS];
     const int32_t ncopy = L < cap ? L : cap;
     if (ncopy <= 0) return GBX_OK;
     LevelRec* recs = new LevelRec[ncopy];
-    const cudaError_t e = cudaMemcpy(recs, G->trace, sizeof(LevelRec) * ncopy, cudaMemcpyDeviceToHost);
+    const cudaError_t e = cudaMemcpy(recs, G->ws.trace, sizeof(LevelRec) * ncopy, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) {
         delete[] recs;
         GBX_CUDA_TRY(e);

@@ -78,6 +78,39 @@ constexpr int kTraceCap = 1 << 16;
 
 // ---------------------------------------------------------------- graph
 
+// Per-run scratch of the persistent kernels and of gbx_mxv.  A graph owns one
+// (used by gbx_bfs, gbx_mxv, gbx_bfs_batch); the server gives each of its slots
+// another, so several batches of the same graph can run at once.
+struct Workspace {
+    int32_t n_cap = 0;  // vertices the buffers below hold
+    uint32_t* bm[4] = {nullptr, nullptr, nullptr, nullptr};  // n-bit bitmaps
+    int32_t* q[2] = {nullptr, nullptr};                       // frontier queues
+    int32_t* qp[2] = {nullptr, nullptr};                      // out-degree prefix per entry
+    int32_t* qd[2] = {nullptr, nullptr};                      // row start minus prefix per entry
+    int32_t* list = nullptr;                                  // n ints (mxv lists, touched lists)
+    int32_t* scan_tmp = nullptr;                              // block sums for scans
+    LevelCtr* ctr = nullptr;                                  // 4 entries
+    GridBar* bar = nullptr;
+    LevelRec* trace = nullptr;                                // kTraceCap records
+    int32_t* status = nullptr;                                // ST_WORDS ints
+    int32_t* flag = nullptr;                                  // small device scratch (mxv decisions)
+    unsigned int bar_parity = 0;  // counter of GridBar the next persistent launch uses
+    // batched multi-source BFS scratch (allocated on first use, grown as needed)
+    unsigned long long* msV = nullptr;  // visited lanes [n][W]
+    unsigned long long* msF = nullptr;  // lanes found at the current level [n][W]
+    unsigned long long* msN = nullptr;  // push accumulation [n][W]
+    int64_t ms_cap_words = 0;
+    int32_t* ms_src = nullptr;  // device copy of the sources
+    int32_t* ms_src_pinned = nullptr;
+    int32_t ms_src_cap = 0;
+    cudaEvent_t ms_src_ready = nullptr;
+    cudaStream_t last_stream = nullptr;
+    int last_traced = 0;
+};
+
+gbx_status workspace_alloc(Workspace& w, int32_t n);
+void workspace_release(Workspace& w);
+
 struct Graph {
     int32_t n = 0;
     int32_t nwords = 0;  // ceil(n / 32)
@@ -96,39 +129,14 @@ struct Graph {
     // pull row reads this dense array instead of a random sector of in_col
     int32_t* first_in = nullptr;
     int32_t* first_out = nullptr;
-    // scratch shared by the operations of this graph (ordered on one stream)
-    uint32_t* bm[4] = {nullptr, nullptr, nullptr, nullptr};  // n-bit bitmaps
-    int32_t* q[2] = {nullptr, nullptr};                       // frontier queues
-    int32_t* qp[2] = {nullptr, nullptr};                      // out-degree prefix per entry
-    int32_t* qd[2] = {nullptr, nullptr};                      // row start minus prefix per entry
-    int32_t* list = nullptr;                                  // n ints (mxv lists)
-    int32_t* scan_tmp = nullptr;                              // block sums for scans
-    LevelCtr* ctr = nullptr;                                  // 4 entries
-    GridBar* bar = nullptr;
-    LevelRec* trace = nullptr;                                // kTraceCap records
-    int32_t* status = nullptr;                                // ST_WORDS ints
-    int32_t* flag = nullptr;                                  // small device scratch (mxv decisions)
+    Workspace ws;  // scratch of the operations called on this graph (ordered on one stream)
     // host-side copies for gbx_bfs_host (allocated on first use)
     int32_t* hdepth[2] = {nullptr, nullptr};
     int32_t* hparent[2] = {nullptr, nullptr};
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t ev_done[2] = {nullptr, nullptr};
     cudaEvent_t ev_copied[2] = {nullptr, nullptr};
-    // BFS launch geometry
-    int bfs_blocks = 0;
-    unsigned int bar_parity = 0;  // counter of GridBar the next persistent launch uses
-    // batched multi-source BFS scratch (allocated on first use, grown as needed)
-    unsigned long long* msV = nullptr;  // visited lanes [n][W]
-    unsigned long long* msF = nullptr;  // lanes found at the current level [n][W]
-    unsigned long long* msN = nullptr;  // push accumulation [n][W]
-    int64_t ms_cap_words = 0;
-    int32_t* ms_src = nullptr;       // device copy of the sources
-    int32_t* ms_src_pinned = nullptr;
-    int32_t ms_src_cap = 0;
-    int ms_blocks = 0;
-    cudaEvent_t ms_src_ready = nullptr;
-    cudaStream_t last_stream = nullptr;
-    int last_traced = 0;
+    int bfs_blocks = 0;  // BFS launch geometry
 };
 
 // ---------------------------------------------------------------- primitives (prims.cu)
@@ -253,12 +261,10 @@ inline gbx_status check_graph(const gbx_graph* g) {
 inline Graph* as_impl(gbx_graph* g) { return reinterpret_cast<Graph*>(g); }
 inline const Graph* as_impl(const gbx_graph* g) { return reinterpret_cast<const Graph*>(g); }
 
-gbx_status graph_scratch_alloc(Graph* g);
-
 // Batched BFS internals (msbfs.cu), shared with the server.
-gbx_status ms_reserve(Graph* G, int32_t S, cudaStream_t s);
+gbx_status ms_reserve(Workspace& w, int32_t n, int32_t S, cudaStream_t s);
 int64_t ms_scratch_bytes(int32_t n, int32_t S);
-gbx_status ms_run(Graph* G, int32_t S, const int32_t* src_dev, void* depth, void* const* rows, int depth16,
-                  const gbx_desc& d, int blocks, cudaStream_t s);
+gbx_status ms_run(Graph* G, Workspace& w, int32_t S, const int32_t* src_dev, void* depth, void* const* rows,
+                  int depth16, const gbx_desc& d, int blocks, cudaStream_t s);
 
 }  // namespace gbx

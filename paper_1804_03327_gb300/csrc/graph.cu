@@ -140,6 +140,32 @@ static gbx_status keys_to_csr(unsigned long long* keys, unsigned long long* alt,
     return GBX_OK;
 }
 
+void workspace_release(Workspace& w) {
+    auto f = [](void* p) {
+        if (p) cudaFree(p);
+    };
+    for (auto& p : w.bm) f(p);
+    for (int i = 0; i < 2; ++i) {
+        f(w.q[i]);
+        f(w.qp[i]);
+        f(w.qd[i]);
+    }
+    f(w.list);
+    f(w.scan_tmp);
+    f(w.ctr);
+    f(w.bar);
+    f(w.trace);
+    f(w.status);
+    f(w.flag);
+    f(w.msV);
+    f(w.msF);
+    f(w.msN);
+    f(w.ms_src);
+    if (w.ms_src_pinned) cudaFreeHost(w.ms_src_pinned);
+    if (w.ms_src_ready) cudaEventDestroy(w.ms_src_ready);
+    w = Workspace{};
+}
+
 static void graph_release(Graph* g) {
     if (!g) return;
     auto f = [](void* p) {
@@ -153,52 +179,37 @@ static void graph_release(Graph* g) {
     if (g->nz_out != g->nz_in) f(g->nz_out);
     if (g->first_out != g->first_in) f(g->first_out);
     f(g->first_in);
-    for (auto& p : g->bm) f(p);
+    workspace_release(g->ws);
     for (int i = 0; i < 2; ++i) {
-        f(g->q[i]);
-        f(g->qp[i]);
-        f(g->qd[i]);
         f(g->hdepth[i]);
         f(g->hparent[i]);
         if (g->ev_done[i]) cudaEventDestroy(g->ev_done[i]);
         if (g->ev_copied[i]) cudaEventDestroy(g->ev_copied[i]);
     }
-    f(g->list);
-    f(g->scan_tmp);
-    f(g->ctr);
-    f(g->bar);
-    f(g->trace);
-    f(g->status);
-    f(g->flag);
-    f(g->msV);
-    f(g->msF);
-    f(g->msN);
-    f(g->ms_src);
-    if (g->ms_src_pinned) cudaFreeHost(g->ms_src_pinned);
-    if (g->ms_src_ready) cudaEventDestroy(g->ms_src_ready);
     if (g->copy_stream) cudaStreamDestroy(g->copy_stream);
     delete g;
 }
 
-gbx_status graph_scratch_alloc(Graph* g) {
-    const size_t nw = (size_t)g->nwords + 1;
-    const size_t nn = (size_t)g->n + 1;
-    for (auto& p : g->bm) GBX_CUDA_TRY(cudaMalloc((void**)&p, sizeof(uint32_t) * nw));
+gbx_status workspace_alloc(Workspace& w, int32_t n) {
+    const size_t nw = (size_t)(n + 31) / 32 + 1;
+    const size_t nn = (size_t)n + 1;
+    w.n_cap = n;
+    for (auto& p : w.bm) GBX_CUDA_TRY(cudaMalloc((void**)&p, sizeof(uint32_t) * nw));
     for (int i = 0; i < 2; ++i) {
-        GBX_CUDA_TRY(cudaMalloc((void**)&g->q[i], sizeof(int32_t) * nn));
-        GBX_CUDA_TRY(cudaMalloc((void**)&g->qp[i], sizeof(int32_t) * nn));
-        GBX_CUDA_TRY(cudaMalloc((void**)&g->qd[i], sizeof(int32_t) * nn));
+        GBX_CUDA_TRY(cudaMalloc((void**)&w.q[i], sizeof(int32_t) * nn));
+        GBX_CUDA_TRY(cudaMalloc((void**)&w.qp[i], sizeof(int32_t) * nn));
+        GBX_CUDA_TRY(cudaMalloc((void**)&w.qd[i], sizeof(int32_t) * nn));
     }
-    GBX_CUDA_TRY(cudaMalloc((void**)&g->list, sizeof(int32_t) * nn));
-    GBX_CUDA_TRY(cudaMalloc((void**)&g->scan_tmp, sizeof(int32_t) * scan_tmp_ints((int64_t)nn)));
-    GBX_CUDA_TRY(cudaMalloc((void**)&g->ctr, sizeof(LevelCtr) * 4));
-    GBX_CUDA_TRY(cudaMalloc((void**)&g->bar, sizeof(GridBar)));
-    GBX_CUDA_TRY(cudaMemset(g->bar, 0, sizeof(GridBar)));
-    GBX_CUDA_TRY(cudaMalloc((void**)&g->trace, sizeof(LevelRec) * kTraceCap));
-    GBX_CUDA_TRY(cudaMalloc((void**)&g->status, sizeof(int32_t) * ST_WORDS));
-    GBX_CUDA_TRY(cudaMemset(g->status, 0, sizeof(int32_t) * ST_WORDS));
-    GBX_CUDA_TRY(cudaMalloc((void**)&g->flag, sizeof(int32_t) * 64));
-    GBX_CUDA_TRY(cudaMemset(g->flag, 0, sizeof(int32_t) * 64));
+    GBX_CUDA_TRY(cudaMalloc((void**)&w.list, sizeof(int32_t) * nn));
+    GBX_CUDA_TRY(cudaMalloc((void**)&w.scan_tmp, sizeof(int32_t) * scan_tmp_ints((int64_t)nn)));
+    GBX_CUDA_TRY(cudaMalloc((void**)&w.ctr, sizeof(LevelCtr) * 4));
+    GBX_CUDA_TRY(cudaMalloc((void**)&w.bar, sizeof(GridBar)));
+    GBX_CUDA_TRY(cudaMemset(w.bar, 0, sizeof(GridBar)));
+    GBX_CUDA_TRY(cudaMalloc((void**)&w.trace, sizeof(LevelRec) * kTraceCap));
+    GBX_CUDA_TRY(cudaMalloc((void**)&w.status, sizeof(int32_t) * ST_WORDS));
+    GBX_CUDA_TRY(cudaMemset(w.status, 0, sizeof(int32_t) * ST_WORDS));
+    GBX_CUDA_TRY(cudaMalloc((void**)&w.flag, sizeof(int32_t) * 64));
+    GBX_CUDA_TRY(cudaMemset(w.flag, 0, sizeof(int32_t) * 64));
     return GBX_OK;
 }
 
@@ -211,7 +222,7 @@ static gbx_status build_impl(Graph* g, int32_t n, int64_t m, const int32_t* src,
     g->n = n;
     g->nwords = (n + 31) / 32;
     g->symmetric = sym;
-    GBX_TRY(graph_scratch_alloc(g));
+    GBX_TRY(workspace_alloc(g->ws, n));
 
     const int64_t K = sym ? 2 * m : m;
     GBX_CHECK(K < ((int64_t)1 << 32), GBX_ERR_OVERFLOW, "too many edge entries (2^32 or more)");
@@ -245,9 +256,9 @@ static gbx_status build_impl(Graph* g, int32_t n, int64_t m, const int32_t* src,
         cudaFreeAsync(alt, s);
         if (own) cudaFreeAsync(own, s);
     };
-    GBX_CUDA_TRY(cudaMemsetAsync(g->status + ST_BADINDEX, 0xff, sizeof(int32_t), s));
-    if (m > 0) make_keys_kernel<<<grid_for(m), 256, 0, s>>>(dsrc, ddst, m, n, b, sym, drop, 0, keys, g->status);
-    e = cudaMemcpyAsync(&bad, g->status + ST_BADINDEX, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    GBX_CUDA_TRY(cudaMemsetAsync(g->ws.status + ST_BADINDEX, 0xff, sizeof(int32_t), s));
+    if (m > 0) make_keys_kernel<<<grid_for(m), 256, 0, s>>>(dsrc, ddst, m, n, b, sym, drop, 0, keys, g->ws.status);
+    e = cudaMemcpyAsync(&bad, g->ws.status + ST_BADINDEX, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         cleanup();
@@ -261,7 +272,7 @@ static gbx_status build_impl(Graph* g, int32_t n, int64_t m, const int32_t* src,
     st = keys_to_csr(keys, alt, K, n, b, &g->out_ptr, &g->out_col, &g->nnz, s);
     if (st == GBX_OK && !sym) {
         // A^T: the same entries with row and column exchanged
-        if (m > 0) make_keys_kernel<<<grid_for(m), 256, 0, s>>>(dsrc, ddst, m, n, b, 0, drop, 1, keys, g->status);
+        if (m > 0) make_keys_kernel<<<grid_for(m), 256, 0, s>>>(dsrc, ddst, m, n, b, 0, drop, 1, keys, g->ws.status);
         int64_t nnz_t = 0;
         st = keys_to_csr(keys, alt, K, n, b, &g->in_ptr, &g->in_col, &nnz_t, s);
         if (st == GBX_OK && nnz_t != g->nnz) {
@@ -372,13 +383,13 @@ extern "C" gbx_status gbx_graph_sync(gbx_graph* g, void* stream) {
     Graph* G = as_impl(g);
     cudaStream_t s = (cudaStream_t)stream;
     GBX_CUDA_TRY(cudaStreamSynchronize(s));
-    if (G->last_stream && G->last_stream != s) GBX_CUDA_TRY(cudaStreamSynchronize(G->last_stream));
+    if (G->ws.last_stream && G->ws.last_stream != s) GBX_CUDA_TRY(cudaStreamSynchronize(G->ws.last_stream));
     int32_t err = 0;
-    GBX_CUDA_TRY(cudaMemcpy(&err, G->status + ST_ERROR, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    GBX_CUDA_TRY(cudaMemcpy(&err, G->ws.status + ST_ERROR, sizeof(int32_t), cudaMemcpyDeviceToHost));
     if (err != 0) {
         // a kernel gave up: clear the error and the barrier it may have left half-arrived
-        GBX_CUDA_TRY(cudaMemset(G->status + ST_ERROR, 0, sizeof(int32_t)));
-        GBX_CUDA_TRY(cudaMemset(G->bar, 0, sizeof(GridBar)));
+        GBX_CUDA_TRY(cudaMemset(G->ws.status + ST_ERROR, 0, sizeof(int32_t)));
+        GBX_CUDA_TRY(cudaMemset(G->ws.bar, 0, sizeof(GridBar)));
         set_error(err == GBX_ERR_TIMEOUT ? "a bounded device-side wait ran out" : "device-side error");
         return (gbx_status)err;
     }

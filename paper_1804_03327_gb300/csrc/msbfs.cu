@@ -489,23 +489,23 @@ __global__ void __launch_bounds__(kMsThreads, 1) ms_bfs_kernel(MsArgs a) {
     }
 }
 
-gbx_status ms_reserve(Graph* G, int32_t S, cudaStream_t s) {
+gbx_status ms_reserve(Workspace& w, int32_t n, int32_t S, cudaStream_t s) {
     const int32_t w_raw = (S + 63) / 64;
     const int cw = w_raw >= 4 ? 4 : (w_raw >= 2 ? 2 : 1);
-    const int64_t need = (int64_t)G->n * ((w_raw + cw - 1) / cw * cw);
-    if (G->ms_cap_words < need) {
-        if (G->msV) {
+    const int64_t need = (int64_t)n * ((w_raw + cw - 1) / cw * cw);
+    if (w.ms_cap_words < need) {
+        if (w.msV) {
             GBX_CUDA_TRY(cudaStreamSynchronize(s));
-            cudaFree(G->msV);
-            cudaFree(G->msF);
-            cudaFree(G->msN);
-            G->msV = G->msF = G->msN = nullptr;
-            G->ms_cap_words = 0;
+            cudaFree(w.msV);
+            cudaFree(w.msF);
+            cudaFree(w.msN);
+            w.msV = w.msF = w.msN = nullptr;
+            w.ms_cap_words = 0;
         }
-        GBX_CUDA_TRY(cudaMalloc((void**)&G->msV, sizeof(unsigned long long) * (size_t)need));
-        GBX_CUDA_TRY(cudaMalloc((void**)&G->msF, sizeof(unsigned long long) * (size_t)need));
-        GBX_CUDA_TRY(cudaMalloc((void**)&G->msN, sizeof(unsigned long long) * (size_t)need));
-        G->ms_cap_words = need;
+        GBX_CUDA_TRY(cudaMalloc((void**)&w.msV, sizeof(unsigned long long) * (size_t)need));
+        GBX_CUDA_TRY(cudaMalloc((void**)&w.msF, sizeof(unsigned long long) * (size_t)need));
+        GBX_CUDA_TRY(cudaMalloc((void**)&w.msN, sizeof(unsigned long long) * (size_t)need));
+        w.ms_cap_words = need;
     }
     return GBX_OK;
 }
@@ -533,12 +533,13 @@ static gbx_status ms_launch(Graph* G, const MsArgs& a0, int blocks, cudaStream_t
 // [S][n] buffer or a device table of S row pointers.  `blocks` > 1 runs the
 // persistent kernel on 1/blocks of the GPU's resident blocks (so that many
 // batches of other graphs fit alongside); scratch must be reserved for S lanes.
-gbx_status ms_run(Graph* G, int32_t S, const int32_t* src_dev, void* depth, void* const* rows, int depth16,
-                  const gbx_desc& d, int blocks, cudaStream_t s) {
+gbx_status ms_run(Graph* G, Workspace& w, int32_t S, const int32_t* src_dev, void* depth, void* const* rows,
+                  int depth16, const gbx_desc& d, int blocks, cudaStream_t s) {
     const int32_t w_raw = (S + 63) / 64;
     const int cw = w_raw >= 4 ? 4 : (w_raw >= 2 ? 2 : 1);
     const int32_t W = (w_raw + cw - 1) / cw * cw;
-    GBX_CHECK(G->ms_cap_words >= (int64_t)G->n * W, GBX_ERR_INVALID_VALUE, "batch scratch not reserved");
+    GBX_CHECK(w.ms_cap_words >= (int64_t)G->n * W && w.n_cap >= G->n, GBX_ERR_INVALID_VALUE,
+              "batch scratch not reserved");
     MsArgs a;
     a.n = G->n;
     a.S = S;
@@ -550,26 +551,26 @@ gbx_status ms_run(Graph* G, int32_t S, const int32_t* src_dev, void* depth, void
     a.in_ptr = G->in_ptr;
     a.in_col = G->in_col;
     a.nz_in = G->nz_in;
-    a.V = G->msV;
-    a.F = G->msF;
-    a.N = G->msN;
-    a.D = G->bm[2];
-    a.T = G->bm[3];
-    a.tlist = G->list;
+    a.V = w.msV;
+    a.F = w.msF;
+    a.N = w.msN;
+    a.D = w.bm[2];
+    a.T = w.bm[3];
+    a.tlist = w.list;
     a.depth = depth;
     a.rows = rows;
     a.depth16 = depth16;
     a.src = src_dev;
     for (int i = 0; i < 2; ++i) {
-        a.q[i] = G->q[i];
-        a.qp[i] = G->qp[i];
-        a.qd[i] = G->qd[i];
+        a.q[i] = w.q[i];
+        a.qp[i] = w.qp[i];
+        a.qd[i] = w.qd[i];
     }
-    a.ctr = G->ctr;
-    a.bar = G->bar;
-    a.bar_parity = G->bar_parity;
-    a.trace = G->trace;
-    a.status = G->status;
+    a.ctr = w.ctr;
+    a.bar = w.bar;
+    a.bar_parity = w.bar_parity;
+    a.trace = w.trace;
+    a.status = w.status;
     a.alpha = d.alpha;
     a.mode = d.direction;
     a.symmetric = G->symmetric;
@@ -578,9 +579,9 @@ gbx_status ms_run(Graph* G, int32_t S, const int32_t* src_dev, void* depth, void
     const gbx_status st = cw == 4 ? ms_launch<4>(G, a, blocks, s)
                                   : (cw == 2 ? ms_launch<2>(G, a, blocks, s) : ms_launch<1>(G, a, blocks, s));
     if (st != GBX_OK) return st;
-    G->bar_parity ^= 1u;
-    G->last_stream = s;
-    G->last_traced = 2;  // batched trace
+    w.bar_parity ^= 1u;
+    w.last_stream = s;
+    w.last_traced = 2;  // batched trace
     return GBX_OK;
 }
 
@@ -606,27 +607,27 @@ extern "C" gbx_status gbx_bfs_batch(gbx_graph* g, const int32_t* sources, int32_
     GBX_CHECK(d.direction >= GBX_DIR_AUTO && d.direction <= GBX_DIR_PULL, GBX_ERR_INVALID_VALUE, "desc.direction");
     GBX_CHECK(d.alpha >= 0.0f && d.alpha == d.alpha, GBX_ERR_INVALID_VALUE, "desc.alpha must be >= 0");
     cudaStream_t s = (cudaStream_t)stream;
-    GBX_TRY(ms_reserve(G, S, s));
-    if (G->ms_src_cap < S) {
-        if (G->ms_src) {
+    GBX_TRY(ms_reserve(G->ws, G->n, S, s));
+    if (G->ws.ms_src_cap < S) {
+        if (G->ws.ms_src) {
             GBX_CUDA_TRY(cudaStreamSynchronize(s));
-            cudaFree(G->ms_src);
-            cudaFreeHost(G->ms_src_pinned);
-            G->ms_src = nullptr;
-            G->ms_src_pinned = nullptr;
+            cudaFree(G->ws.ms_src);
+            cudaFreeHost(G->ws.ms_src_pinned);
+            G->ws.ms_src = nullptr;
+            G->ws.ms_src_pinned = nullptr;
         }
-        GBX_CUDA_TRY(cudaMalloc((void**)&G->ms_src, sizeof(int32_t) * (size_t)S));
-        GBX_CUDA_TRY(cudaMallocHost((void**)&G->ms_src_pinned, sizeof(int32_t) * (size_t)S));
-        G->ms_src_cap = S;
+        GBX_CUDA_TRY(cudaMalloc((void**)&G->ws.ms_src, sizeof(int32_t) * (size_t)S));
+        GBX_CUDA_TRY(cudaMallocHost((void**)&G->ws.ms_src_pinned, sizeof(int32_t) * (size_t)S));
+        G->ws.ms_src_cap = S;
     }
-    if (!G->ms_src_ready) GBX_CUDA_TRY(cudaEventCreateWithFlags(&G->ms_src_ready, cudaEventDisableTiming));
+    if (!G->ws.ms_src_ready) GBX_CUDA_TRY(cudaEventCreateWithFlags(&G->ws.ms_src_ready, cudaEventDisableTiming));
     // sources: pinned staging, then one async copy (the staging buffer is reused only
     // after the previous copy has completed)
-    GBX_CUDA_TRY(cudaEventSynchronize(G->ms_src_ready));
-    for (int32_t k = 0; k < S; ++k) G->ms_src_pinned[k] = sources[k];
-    GBX_CUDA_TRY(cudaMemcpyAsync(G->ms_src, G->ms_src_pinned, sizeof(int32_t) * (size_t)S, cudaMemcpyHostToDevice, s));
-    GBX_CUDA_TRY(cudaEventRecord(G->ms_src_ready, s));
-    return ms_run(G, S, G->ms_src, depth, nullptr, depth_type == GBX_DEPTH_I16 ? 1 : 0, d, 0, s);
+    GBX_CUDA_TRY(cudaEventSynchronize(G->ws.ms_src_ready));
+    for (int32_t k = 0; k < S; ++k) G->ws.ms_src_pinned[k] = sources[k];
+    GBX_CUDA_TRY(cudaMemcpyAsync(G->ws.ms_src, G->ws.ms_src_pinned, sizeof(int32_t) * (size_t)S, cudaMemcpyHostToDevice, s));
+    GBX_CUDA_TRY(cudaEventRecord(G->ws.ms_src_ready, s));
+    return ms_run(G, G->ws, S, G->ws.ms_src, depth, nullptr, depth_type == GBX_DEPTH_I16 ? 1 : 0, d, 0, s);
 }
 
 extern "C" gbx_status gbx_bfs_batch_trace(gbx_graph* g, gbx_level* levels, int32_t cap, int32_t* nlevels) {
@@ -635,17 +636,17 @@ extern "C" gbx_status gbx_bfs_batch_trace(gbx_graph* g, gbx_level* levels, int32
     Graph* G = as_impl(g);
     GBX_CHECK(nlevels != nullptr, GBX_ERR_NULL_POINTER, "nlevels is NULL");
     GBX_CHECK(cap == 0 || levels != nullptr, GBX_ERR_NULL_POINTER, "levels is NULL");
-    GBX_CHECK(G->last_traced == 2, GBX_ERR_INVALID_VALUE, "the last run on this graph was not a batched BFS");
-    if (G->last_stream) GBX_CUDA_TRY(cudaStreamSynchronize(G->last_stream));
+    GBX_CHECK(G->ws.last_traced == 2, GBX_ERR_INVALID_VALUE, "the last run on this graph was not a batched BFS");
+    if (G->ws.last_stream) GBX_CUDA_TRY(cudaStreamSynchronize(G->ws.last_stream));
     int32_t st[ST_WORDS];
-    GBX_CUDA_TRY(cudaMemcpy(st, G->status, sizeof(st), cudaMemcpyDeviceToHost));
+    GBX_CUDA_TRY(cudaMemcpy(st, G->ws.status, sizeof(st), cudaMemcpyDeviceToHost));
     GBX_CHECK(st[ST_ERROR] == 0, (gbx_status)st[ST_ERROR], "the last batched BFS recorded a device-side error");
     *nlevels = st[ST_LEVELS];
     const int32_t L = st[ST_LEVELS] < kTraceCap ? st[ST_LEVELS] : kTraceCap;
     const int32_t ncopy = L < cap ? L : cap;
     if (ncopy <= 0) return GBX_OK;
     LevelRec* recs = new LevelRec[ncopy];
-    const cudaError_t e = cudaMemcpy(recs, G->trace, sizeof(LevelRec) * ncopy, cudaMemcpyDeviceToHost);
+    const cudaError_t e = cudaMemcpy(recs, G->ws.trace, sizeof(LevelRec) * ncopy, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) {
         delete[] recs;
         GBX_CUDA_TRY(e);

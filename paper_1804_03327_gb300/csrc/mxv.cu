@@ -239,12 +239,12 @@ extern "C" gbx_status gbx_mxv(gbx_vector* w, const gbx_vector* mask, int32_t sem
     const int32_t* push_ptr = d.transpose ? G->out_ptr : G->in_ptr;
     const int32_t* push_col = d.transpose ? G->out_col : G->in_col;
 
-    uint32_t* ubm = G->bm[0];
-    uint32_t* pass = G->bm[1];
-    uint32_t* R = G->bm[2];
-    int32_t* list_count = G->flag + 0;
-    int32_t* dflag = G->flag + 1;
-    MxvStats* stats = d.trace ? reinterpret_cast<MxvStats*>(G->ctr + 3) : nullptr;
+    uint32_t* ubm = G->ws.bm[0];
+    uint32_t* pass = G->ws.bm[1];
+    uint32_t* R = G->ws.bm[2];
+    int32_t* list_count = G->ws.flag + 0;
+    int32_t* dflag = G->ws.flag + 1;
+    MxvStats* stats = d.trace ? reinterpret_cast<MxvStats*>(G->ws.ctr + 3) : nullptr;
     if (stats) zero_stats_kernel<<<1, 1, 0, s>>>(stats);
 
     const int dir = d.direction;
@@ -258,8 +258,8 @@ extern "C" gbx_status gbx_mxv(gbx_vector* w, const gbx_vector* mask, int32_t sem
     if (u->format == GBX_DENSE) {
         GBX_TRY(pack_dense_to_bitmap((const uint8_t*)u->data, n, 0, ubm, s));
         if (want_push) {
-            GBX_TRY(bitmap_to_list(ubm, n, G->list, list_count, G->qd[0], G->scan_tmp, s));
-            ulist = G->list;
+            GBX_TRY(bitmap_to_list(ubm, n, G->ws.list, list_count, G->ws.qd[0], G->ws.scan_tmp, s));
+            ulist = G->ws.list;
             ucount = list_count;
         }
     } else {
@@ -293,11 +293,11 @@ extern "C" gbx_status gbx_mxv(gbx_vector* w, const gbx_vector* mask, int32_t sem
             flag = dflag;
         }
         if (want_push) {
-            int32_t* deg = G->q[0];
-            int32_t* pre = G->qp[0];
+            int32_t* deg = G->ws.q[0];
+            int32_t* pre = G->ws.qp[0];
             mxv_degrees_kernel<<<max(1u, min(div_up(n, 256), 152u * 16)), 256, 0, s>>>(push_ptr, ulist, ucount, ucap,
                                                                                     n, deg, flag);
-            GBX_TRY(exclusive_scan_i32(deg, pre, n, ucount, G->scan_tmp, s));
+            GBX_TRY(exclusive_scan_i32(deg, pre, n, ucount, G->ws.scan_tmp, s));
             mxv_push_kernel<<<G->num_sms * 8, kMxvThreads, 0, s>>>(push_ptr, push_col,
                                                                     ulist, ucount, n, pre, pass_bm, R, flag, stats);
         }
@@ -311,10 +311,10 @@ extern "C" gbx_status gbx_mxv(gbx_vector* w, const gbx_vector* mask, int32_t sem
         GBX_TRY(bitmap_to_dense(R, n, d.accum ? (const uint8_t*)w->data : nullptr, (uint8_t*)w->data, s));
     } else {
         if (d.accum) GBX_TRY(scatter_list_to_bitmap((const int32_t*)w->data, w->nnz, w->capacity, n, R, s));
-        GBX_TRY(bitmap_to_list(R, n, (int32_t*)w->data, w->nnz, G->qd[1], G->scan_tmp, s));
+        GBX_TRY(bitmap_to_list(R, n, (int32_t*)w->data, w->nnz, G->ws.qd[1], G->ws.scan_tmp, s));
     }
     GBX_CUDA_TRY(cudaGetLastError());
-    G->last_stream = s;
+    G->ws.last_stream = s;
     return GBX_OK;
 }
 
@@ -323,9 +323,9 @@ extern "C" gbx_status gbx_mxv_stats(const gbx_graph* A, int64_t* rows, int64_t* 
     clear_error();
     GBX_TRY(check_graph(A));
     const Graph* G = as_impl(A);
-    if (G->last_stream) GBX_CUDA_TRY(cudaStreamSynchronize(G->last_stream));
+    if (G->ws.last_stream) GBX_CUDA_TRY(cudaStreamSynchronize(G->ws.last_stream));
     MxvStats st;
-    GBX_CUDA_TRY(cudaMemcpy(&st, G->ctr + 3, sizeof(st), cudaMemcpyDeviceToHost));
+    GBX_CUDA_TRY(cudaMemcpy(&st, G->ws.ctr + 3, sizeof(st), cudaMemcpyDeviceToHost));
     if (rows) *rows = (int64_t)st.rows;
     if (examined) *examined = (int64_t)st.exam;
     if (u_nnz) *u_nnz = (int64_t)st.ucount;

@@ -1,17 +1,17 @@
 // Continuous-batching BFS server over several resident graphs.
 //
 // Queries (graph, source, output row) queue per graph.  A fixed set of slots --
-// each a CUDA stream with its own staging buffers and completion event -- runs
-// batches: whenever a slot is free, the graph whose oldest query has waited
-// longest (and that has no batch in flight: a graph's scratch serves one batch
-// at a time) sends up to its lane width of queued queries as one batched BFS
-// (gbx_bfs_batch's kernel), every lane writing straight into its query's output
-// row.  Each slot's persistent kernel gets 1/slots of the GPU's resident blocks,
-// so batches of different graphs run side by side.  Queries that arrive while
-// batches are in flight join the next batch of their graph as soon as a slot
-// frees up.  Admission: a graph's lane width is capped so that the batch scratch
-// of all graphs stays within the memory budget, and submissions beyond
-// max_pending queued queries are refused with GBX_ERR_BUSY.
+// each a CUDA stream with its own workspace (the persistent kernels' scratch),
+// staging buffers and completion event -- runs batches: whenever a slot is free,
+// the graph whose oldest query has waited longest sends up to its lane width of
+// queued queries as one batched BFS (gbx_bfs_batch's kernel), every lane writing
+// straight into its query's output row.  Each slot's persistent kernel gets
+// 1/slots of the GPU's resident blocks, so batches -- of different graphs or of
+// the same graph -- run side by side.  Queries that arrive while batches are in
+// flight join the next batch as soon as a slot frees up.  Admission: a graph's
+// lane width is capped so that the slots' batch scratch stays within the memory
+// budget, and submissions beyond max_pending queued queries are refused with
+// GBX_ERR_BUSY.
 #include <chrono>
 #include <deque>
 #include <mutex>
@@ -38,6 +38,7 @@ struct Slot {
     int32_t* src_pinned = nullptr;
     void** rows_pinned = nullptr;
     int32_t* status_pinned = nullptr;
+    Workspace ws;
     std::vector<Query> batch;
     int graph = -1;
     bool busy = false;
@@ -47,7 +48,6 @@ struct Slot {
 struct GraphEntry {
     Graph* g = nullptr;
     int32_t lanes = 0;
-    bool running = false;
     std::deque<Query> pending;
 };
 
@@ -55,7 +55,7 @@ struct Server {
     gbx_server_config cfg;
     std::vector<GraphEntry> graphs;
     std::vector<Slot> slots;
-    int64_t scratch_bytes = 0;
+    int64_t scratch_bytes = 0;  // batch scratch of one slot (all slots hold the same)
     int64_t queued = 0;
     int64_t rejected = 0;
     std::chrono::steady_clock::time_point t0;
@@ -78,11 +78,12 @@ static void server_release(Server* S) {
         if (sl.src_pinned) cudaFreeHost(sl.src_pinned);
         if (sl.rows_pinned) cudaFreeHost(sl.rows_pinned);
         if (sl.status_pinned) cudaFreeHost(sl.status_pinned);
+        workspace_release(sl.ws);
     }
     delete S;
 }
 
-// Completed batches -> completion records; the graph becomes free again.
+// Completed batches -> completion records; the slot becomes free again.
 static gbx_status reap(Server* S) {
     for (Slot& sl : S->slots) {
         if (!sl.busy) continue;
@@ -91,10 +92,9 @@ static gbx_status reap(Server* S) {
         GBX_CUDA_TRY(q);
         const double t = S->now();
         const int32_t err = sl.status_pinned[ST_ERROR];
-        GraphEntry& ge = S->graphs[sl.graph];
         if (err != 0) {  // clear the recorded error and the barrier the kernel may have left
-            GBX_CUDA_TRY(cudaMemsetAsync(ge.g->status + ST_ERROR, 0, sizeof(int32_t), sl.stream));
-            GBX_CUDA_TRY(cudaMemsetAsync(ge.g->bar, 0, sizeof(GridBar), sl.stream));
+            GBX_CUDA_TRY(cudaMemsetAsync(sl.ws.status + ST_ERROR, 0, sizeof(int32_t), sl.stream));
+            GBX_CUDA_TRY(cudaMemsetAsync(sl.ws.bar, 0, sizeof(GridBar), sl.stream));
             GBX_CUDA_TRY(cudaStreamSynchronize(sl.stream));
         }
         for (const Query& qq : sl.batch) {
@@ -112,7 +112,6 @@ static gbx_status reap(Server* S) {
         }
         sl.batch.clear();
         sl.busy = false;
-        ge.running = false;
     }
     return GBX_OK;
 }
@@ -125,7 +124,7 @@ static gbx_status dispatch(Server* S) {
         double best_t = 0.0;
         for (int i = 0; i < (int)S->graphs.size(); ++i) {
             const GraphEntry& ge = S->graphs[i];
-            if (ge.running || ge.pending.empty()) continue;
+            if (ge.pending.empty()) continue;
             if (best < 0 || ge.pending.front().t_submit < best_t) {
                 best = i;
                 best_t = ge.pending.front().t_submit;
@@ -149,14 +148,13 @@ static gbx_status dispatch(Server* S) {
         gbx_desc_init(&d);
         d.alpha = S->cfg.alpha;
         sl.t_launch = S->now();
-        GBX_TRY(ms_run(ge.g, nb, sl.src_dev, nullptr, sl.rows_dev, S->cfg.depth_type == GBX_DEPTH_I16 ? 1 : 0, d,
-                       (int)S->slots.size(), sl.stream));
-        GBX_CUDA_TRY(cudaMemcpyAsync(sl.status_pinned, ge.g->status, sizeof(int32_t) * ST_WORDS,
+        GBX_TRY(ms_run(ge.g, sl.ws, nb, sl.src_dev, nullptr, sl.rows_dev, S->cfg.depth_type == GBX_DEPTH_I16 ? 1 : 0,
+                       d, (int)S->slots.size(), sl.stream));
+        GBX_CUDA_TRY(cudaMemcpyAsync(sl.status_pinned, sl.ws.status, sizeof(int32_t) * ST_WORDS,
                                      cudaMemcpyDeviceToHost, sl.stream));
         GBX_CUDA_TRY(cudaEventRecord(sl.done, sl.stream));
         sl.graph = best;
         sl.busy = true;
-        ge.running = true;
     }
     return GBX_OK;
 }
@@ -221,15 +219,32 @@ extern "C" gbx_status gbx_server_add_graph(gbx_server* srv, gbx_graph* g, int32_
     std::lock_guard<std::mutex> lock(S->mu);
     Graph* G = as_impl(g);
     for (const GraphEntry& ge : S->graphs) GBX_CHECK(ge.g != G, GBX_ERR_INVALID_VALUE, "graph already added");
-    // lane width: the largest multiple of 64 (or max_batch) whose scratch fits the budget
+    const int64_t nslots = (int64_t)S->slots.size();
+    // lane width: the largest multiple of 64 (or max_batch) whose scratch, held once
+    // per slot, fits the budget together with what the other graphs need
     int32_t lanes = S->cfg.max_batch;
     if (S->cfg.memory_budget > 0) {
-        while (lanes > 0 && S->scratch_bytes + ms_scratch_bytes(G->n, lanes) > S->cfg.memory_budget)
-            lanes = lanes > 64 ? (lanes - 1) / 64 * 64 : lanes - 1;
+        auto need = [&](int32_t l) {
+            const int64_t b = ms_scratch_bytes(G->n, l);
+            return nslots * (b > S->scratch_bytes ? b : S->scratch_bytes);
+        };
+        while (lanes > 0 && need(lanes) > S->cfg.memory_budget) lanes = lanes > 64 ? (lanes - 1) / 64 * 64 : lanes - 1;
         GBX_CHECK(lanes >= 1, GBX_ERR_OUT_OF_MEMORY, "memory budget too small for this graph");
     }
-    GBX_TRY(ms_reserve(G, lanes, S->slots[0].stream));
-    S->scratch_bytes += ms_scratch_bytes(G->n, lanes);
+    for (Slot& sl : S->slots) {
+        if (sl.ws.n_cap < G->n) {  // grow the slot's workspace to this graph's size
+            GBX_CUDA_TRY(cudaStreamSynchronize(sl.stream));
+            const int64_t cap = sl.ws.ms_cap_words;
+            workspace_release(sl.ws);
+            GBX_TRY(workspace_alloc(sl.ws, G->n));
+            (void)cap;
+        }
+        GBX_TRY(ms_reserve(sl.ws, G->n, lanes, sl.stream));
+    }
+    for (const GraphEntry& ge : S->graphs)
+        for (Slot& sl : S->slots) GBX_TRY(ms_reserve(sl.ws, ge.g->n, ge.lanes, sl.stream));
+    const int64_t b = ms_scratch_bytes(G->n, lanes);
+    if (b > S->scratch_bytes) S->scratch_bytes = b;
     GraphEntry ge;
     ge.g = G;
     ge.lanes = lanes;
@@ -296,7 +311,7 @@ extern "C" gbx_status gbx_server_stats(gbx_server* srv, int64_t* queued, int32_t
     if (queued) *queued = S->queued;
     if (in_flight) *in_flight = busy;
     if (rejected) *rejected = S->rejected;
-    if (scratch_bytes) *scratch_bytes = S->scratch_bytes;
+    if (scratch_bytes) *scratch_bytes = S->scratch_bytes * (int64_t)S->slots.size();
     return GBX_OK;
 }
 
