@@ -259,9 +259,9 @@ def batched_measurements(g, n, sources, reached, single_value, args):
     import synth
     from paper_1804_03327_gb300 import gbx
 
-    bdesc = gbx.desc_init(alpha=0.05)
-
-    def time_batch(gg, srcs, nn, reps=3):
+    def time_batch(gg, srcs, nn, reps=3, tune_srcs=None):
+        # batch descriptor autotuned on other seeded sources of the same graph and width
+        bdesc, _ = gbx.autotune(gg, gbx.TUNE_BATCH, tune_srcs if tune_srcs is not None else srcs)
         depth = torch.empty((len(srcs), nn), dtype=torch.int16, device="cuda")
         gbx.bfs_batch(gg, srcs, depth, bdesc)
         gbx.graph_sync(gg)
@@ -286,7 +286,8 @@ def batched_measurements(g, n, sources, reached, single_value, args):
         return out
 
     res = {}
-    t = time_batch(g, sources, n)
+    import synth as _synth
+    t = time_batch(g, sources, n, tune_srcs=_synth.sources(n, *args._edges, len(sources), seed=SEED + 200))
     v = sum(reached) / t / 1e9
     res["same_sources_as_one_batch"] = {"workload": WORKLOAD, "S": len(sources), "ms": t * 1e3, "value": v,
                                         "unit": UNIT, "vs_single_source": v / single_value}
@@ -297,6 +298,7 @@ def batched_measurements(g, n, sources, reached, single_value, args):
         gg = gbx.graph_build(nn, ss, dd)
         widths = (64, 256, 1024) if name.startswith("rmat") else (64,)
         all_src = synth.sources(nn, ss, dd, max(widths), seed=SEED)
+        tune_all = synth.sources(nn, ss, dd, max(widths), seed=SEED + 300)
         # single-source reference on the first 64 of these sources
         d = torch.empty(nn, dtype=torch.int32, device="cuda")
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -309,7 +311,7 @@ def batched_measurements(g, n, sources, reached, single_value, args):
         single_s = e0.elapsed_time(e1) / 1e3 / 64
         reach = reached_of(gg, all_src, nn)
         for S in widths:
-            tb = time_batch(gg, all_src[:S], nn, reps=1 if name.startswith("grid") else 3)
+            tb = time_batch(gg, all_src[:S], nn, reps=1 if name.startswith("grid") else 3, tune_srcs=tune_all[:S])
             edges = sum(reach[:S])
             cfg4.append({"graph": name, "S": S, "ms": tb * 1e3, "value": edges / tb / 1e9, "unit": UNIT,
                          "single_source_value": edges / (single_s * S) / 1e9,
@@ -321,7 +323,10 @@ def batched_measurements(g, n, sources, reached, single_value, args):
 
 def served_measurement(main_graph, args):
     """Poisson arrivals of single-source queries over six resident graphs,
-    continuously batched by gbx_server; p50/p99 latency and GTEPS."""
+    continuously batched by gbx_server; p50/p99 latency and GTEPS.  Runs at the
+    configured rate (20k queries/s: far above what one GPU can absorb for this
+    mix, so it measures the saturated throughput) and again at half of that
+    measured throughput, where queues stay bounded and latency is meaningful."""
     import torch
 
     import synth
@@ -354,63 +359,74 @@ def served_measurement(main_graph, args):
                 if dn[int(s1)] >= 0:
                     reach[int(s1)] = e
         graphs.append({"name": name, "g": g, "n": n, "cand": cand, "reach": reach, "own": gen is not None})
-    srv = gbx.Server(max_batch=64, slots=8, depth_type=gbx.DEPTH_I16, max_pending=1 << 16)
+    slots = 8
+    srv = gbx.Server(max_batch=64, slots=slots, depth_type=gbx.DEPTH_I16, max_pending=1 << 16)
+    rows = 2048
     for gi in graphs:
         gi["id"] = srv.add_graph(gi["g"])
-        rows = 2048
         gi["pool"] = torch.empty((rows, gi["n"]), dtype=torch.int16, device="cuda")
-        gi["free"] = list(range(rows))
-    rng = np.random.default_rng(SEED)
-    warm, span = 0.5, args.serve_seconds
-    t_arr = np.cumsum(rng.exponential(1.0 / args.serve_rate, size=int(args.serve_rate * (warm + span) * 1.2)))
-    t_arr = t_arr[t_arr < warm + span]
-    which = rng.integers(0, len(graphs), size=len(t_arr))
-    pick = rng.integers(0, 256, size=len(t_arr))
-    inflight = {}
-    lat, edges_done, refused, waited = [], 0, 0, 0
-    t0 = time.perf_counter()
-    i = 0
-    done_n = 0
-    while i < len(t_arr) or inflight:
-        now = time.perf_counter() - t0
-        while i < len(t_arr) and t_arr[i] <= now:
-            gi = graphs[which[i]]
-            if not gi["free"]:
-                waited += 1
-                break  # client has no free output row for this graph: wait for completions
-            slot = gi["free"].pop()
-            s0 = int(gi["cand"][pick[i]])
-            if srv.submit(gi["id"], s0, gi["pool"][slot], tag=i):
-                inflight[i] = (gi, slot, s0)
-            else:
+
+    def run(rate, seed):
+        for gi in graphs:
+            gi["free"] = list(range(rows))
+        rng = np.random.default_rng(seed)
+        warm, span = 0.5, args.serve_seconds
+        t_arr = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * (warm + span) * 1.3) + 16))
+        t_arr = t_arr[t_arr < warm + span]
+        which = rng.integers(0, len(graphs), size=len(t_arr))
+        pick = rng.integers(0, 256, size=len(t_arr))
+        inflight = {}
+        lat, edges_done, refused, waited, done_n = [], 0, 0, 0, 0
+        t0 = time.perf_counter()
+        i = 0
+        while i < len(t_arr) or inflight:
+            now = time.perf_counter() - t0
+            while i < len(t_arr) and t_arr[i] <= now:
+                gi = graphs[which[i]]
+                if not gi["free"]:
+                    waited += 1
+                    break  # client has no free output row for this graph: wait for completions
+                slot = gi["free"].pop()
+                s0 = int(gi["cand"][pick[i]])
+                if srv.submit(gi["id"], s0, gi["pool"][slot], tag=i):
+                    inflight[i] = (gi, slot, s0)
+                else:
+                    gi["free"].append(slot)
+                    refused += 1
+                i += 1
+            cs = srv.poll()
+            t_seen = time.perf_counter() - t0
+            for c in cs:
+                gi, slot, s0 = inflight.pop(c.tag)
                 gi["free"].append(slot)
-                refused += 1
-            i += 1
-        cs = srv.poll()
-        t_seen = time.perf_counter() - t0
-        for c in cs:
-            gi, slot, s0 = inflight.pop(c.tag)
-            gi["free"].append(slot)
-            done_n += 1
-            if t_arr[c.tag] >= warm:
-                lat.append(t_seen - t_arr[c.tag])  # arrival (scheduled) -> completion seen
-                edges_done += gi["reach"].get(s0, 0)
-    wall = time.perf_counter() - t0
+                done_n += 1
+                if t_arr[c.tag] >= warm:
+                    lat.append(t_seen - t_arr[c.tag])  # arrival (scheduled) -> completion seen
+                    edges_done += gi["reach"].get(s0, 0)
+        wall = time.perf_counter() - t0
+        lat = np.array(lat) if lat else np.array([0.0])
+        window = wall - warm
+        return {"arrival_rate_qps": rate, "arrivals": int(len(t_arr)), "measured_queries": int(len(lat)),
+                "completed": done_n, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                "p99_ms": float(np.percentile(lat, 99) * 1e3), "value": edges_done / window / 1e9, "unit": UNIT,
+                "throughput_qps": len(lat) / window, "refused": refused, "client_waits": waited}
+
+    saturated = run(args.serve_rate, SEED)
+    sustainable = run(max(1.0, 0.5 * saturated["throughput_qps"]), SEED + 1)
     st = srv.stats()
     srv.destroy()
     for gi in graphs:
         if gi["own"]:
             gi["g"].free()
-    lat = np.array(lat) if lat else np.array([0.0])
-    measured_window = wall - warm
-    return {"graphs": [gi["name"] for gi in graphs], "arrival_rate_qps": args.serve_rate,
-            "arrivals": int(len(t_arr)), "measured_queries": int(len(lat)), "completed": done_n,
-            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-            "value": edges_done / measured_window / 1e9, "unit": UNIT,
-            "throughput_qps": len(lat) / measured_window, "refused": refused, "client_waits": waited,
-            "server": {"slots": 8, "max_batch": 64, "depth": "int16", "scratch_bytes": st["scratch_bytes"]},
-            "note": "latency = scheduled arrival -> completion observed by the client's poll; GTEPS and "
-                    "throughput over queries arriving after the 0.5 s warm-up"}
+    mean_edges = float(np.mean([np.mean(list(gi["reach"].values())) for gi in graphs]))
+    return {"graphs": [gi["name"] for gi in graphs], "at_configured_rate": saturated,
+            "at_half_saturated_throughput": sustainable,
+            "mean_reached_edges_per_query": mean_edges,
+            "gteps_needed_for_configured_rate": args.serve_rate * mean_edges / 1e9,
+            "server": {"slots": slots, "max_batch": 64, "depth": "int16", "scratch_bytes": st["scratch_bytes"]},
+            "note": "latency = scheduled arrival -> completion seen by the client's poll; rates and GTEPS over "
+                    "queries arriving after a 0.5 s warm-up; graph uniform per query, source uniform over 256 "
+                    "seeded candidates per graph"}
 
 
 def run_ours(args):
@@ -435,9 +451,14 @@ def run_ours(args):
     depth = torch.empty((S, n), dtype=torch.int32, device="cuda")
     parent = torch.empty((S, n), dtype=torch.int32, device="cuda")
 
+    # descriptor: autotuned on 16 other seeded sources of the same graph (not the measured ones)
+    tune_src = synth.sources(n, src, dst, 16, seed=SEED + 100)
+    desc, tune_ms = gbx.autotune(g, gbx.TUNE_BFS, tune_src)
     # one traced pass (untimed): per-source level counts -> reached edges and algorithmic bytes
     reached, balg, traces = [], [], []
-    dtrace = gbx.desc_init(trace=1)
+    dtrace = gbx.Desc.from_buffer_copy(desc)
+    dtrace.trace = 1
+    default_desc = gbx.desc_init()
     for k, s in enumerate(sources):
         gbx.bfs(g, int(s), depth[k], parent[k], dtrace)
         tr = gbx.bfs_trace(g)
@@ -445,7 +466,6 @@ def run_ours(args):
         reached.append(roofline.reached_edges(tr))
         balg.append(roofline.bfs_bytes(tr, n))
     gbx.graph_sync(g)
-    desc = gbx.desc_init()
     step_edges = sum(reached)
 
     def step(ev=None):
@@ -488,6 +508,17 @@ def run_ours(args):
 
     # verify the timed outputs against the traced pass (depth is deterministic)
     per_src_gteps = [reached[k] / (float(np.median(launch_ms[:, k])) / 1e3) / 1e9 for k in range(S)]
+    # the paper's own descriptor (ratio rule, alpha = beta = 0.01), same sources, beside the tuned one
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for k2, s2 in enumerate(sources):
+        gbx.bfs(g, int(s2), depth[k2], parent[k2], default_desc)
+    e0.record(stream)
+    for _ in range(max(1, args.steps // 2)):
+        for k2, s2 in enumerate(sources):
+            gbx.bfs(g, int(s2), depth[k2], parent[k2], default_desc)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    default_value = step_edges * max(1, args.steps // 2) / (e0.elapsed_time(e1) / 1e3) / 1e9
     peak, peak_kind = peaks()
     mean_bytes = float(np.mean(balg))
     achieved = mean_bytes / mean_launch_s / 1e9
@@ -516,6 +547,7 @@ def run_ours(args):
                "steps": e_steps, "api": "gbx_bfs_host (pinned host depth+parent, D2H overlapped with the next BFS)"}
 
     batched = None
+    args._edges = (src, dst)
     if rank == 0 and not args.no_batched:
         batched = batched_measurements(g, n, sources, reached, value / world, args)
     served = None
@@ -551,6 +583,8 @@ def run_ours(args):
         "gpu_launches": args.steps * S,
         "clocks": clock_info,
         "gteps_paper_convention": int(nnz) * S * args.steps * world / elapsed / 1e9,
+        "descriptor": {"autotuned_on": "16 other seeded sources of the same graph", **gbx.desc_dict(desc)},
+        "value_with_paper_default_descriptor": default_value,
         "per_source_gteps": {"hmean": float(len(per_src_gteps) / np.sum(1.0 / np.array(per_src_gteps))),
                              "median": float(np.median(per_src_gteps))},
         "schedule_example": dirs[0],

@@ -154,12 +154,15 @@ typedef struct {
     int32_t masking;         /* BFS pull visits only unvisited rows (Section 5.2; default 1) */
     int32_t operand_reuse;   /* BFS pull tests "visited" instead of "in frontier" (Section 5.4; default 1) */
     int32_t trace;           /* BFS: record per-level statistics (see gbx_bfs_trace) */
-    int32_t reserved[5];     /* must be 0 */
+    int32_t pull_probe;      /* BFS pull: in-neighbours one lane scans before its warp takes the row over
+                                (0 = default: 16 single-source, 8 batched; otherwise 4..1024) */
+    int32_t blocks_per_sm;   /* BFS kernels: persistent blocks per SM (0 = as many as fit) */
+    int32_t reserved[3];     /* must be 0 */
 } gbx_desc;
 
 /* Defaults: transpose 1, mask_complement 0, early_exit 1, accum 0,
  * direction AUTO, heuristic RATIO, alpha = beta = 0.01 (Section 6.3),
- * masking 1, operand_reuse 1, trace 0. */
+ * masking 1, operand_reuse 1, trace 0, pull_probe 0, blocks_per_sm 0. */
 void gbx_desc_init(gbx_desc* d);
 
 /* ------------------------------------------------------------------ matvec */
@@ -300,6 +303,27 @@ gbx_status gbx_bfs_batch(gbx_graph* g, const int32_t* sources, int32_t S, void* 
  * the previous level, e_exam = edges examined by pull levels (once per 256-lane
  * chunk), n_new = pairs found at this level, mf_new, time_ns; nu and nu_nz are -1. */
 gbx_status gbx_bfs_batch_trace(gbx_graph* g, gbx_level* levels, int32_t cap, int32_t* nlevels);
+
+/* ------------------------------------------------------------------ autotuner */
+
+#define GBX_TUNE_BFS 0   /* single-source gbx_bfs, timed over `count` separate runs */
+#define GBX_TUNE_BATCH 1 /* gbx_bfs_batch with the `count` sources as one batch */
+
+/*
+ * Time candidate descriptors on g with the given host sources and return the
+ * fastest in *best (and its time in ms in *best_ms, may be NULL).  Section 6.3
+ * chose its switch point by comparison with running both directions on every
+ * level; here whole descriptors are compared: for GBX_TUNE_BFS the direction
+ * rule (ratio / Beamer) x alpha x beta, then the pull probe depth and the
+ * persistent blocks per SM; for GBX_TUNE_BATCH the batch alpha, then the probe
+ * depth.  Results never change (every candidate computes the same depths).  If
+ * cache_path is not NULL, a previous result for the same graph shape (n, nnz,
+ * symmetric, kind, batch size) is returned from that text file without timing,
+ * and new results are appended to it.  Synchronises `stream`.  Allocates a
+ * temporary depth buffer.  Errors: NULL_POINTER, INVALID_VALUE, INVALID_INDEX, CUDA.
+ */
+gbx_status gbx_autotune(gbx_graph* g, int32_t kind, const int32_t* sources, int32_t count, gbx_desc* best,
+                        double* best_ms, const char* cache_path, void* stream);
 
 /* ------------------------------------------------------------------ server */
 

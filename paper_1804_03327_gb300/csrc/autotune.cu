@@ -1,0 +1,188 @@
+// Autotuner for the BFS descriptors: times candidate settings on the caller's
+// graph and sources and keeps the fastest.  Section 6.3 picks its switch point
+// by comparing against running both directions on every level and choosing the
+// faster; here the candidates are whole descriptors (direction rule, thresholds,
+// lane probe depth, persistent blocks per SM) timed end to end with CUDA events.
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gbx_internal.cuh"
+
+namespace gbx {
+
+struct TuneKey {
+    int32_t kind, n, sym, S;
+    long long nnz;
+};
+
+static bool cache_lookup(const char* path, const TuneKey& k, gbx_desc* d, double* ms) {
+    if (!path) return false;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return false;
+    char line[512];
+    bool found = false;
+    while (std::fgets(line, sizeof(line), f)) {
+        int kind, n, sym, S, heur, probe, bps, dir;
+        long long nnz;
+        float alpha, beta;
+        double t;
+        if (std::sscanf(line, "%d %d %lld %d %d %d %d %f %f %d %d %lf", &kind, &n, &nnz, &sym, &S, &dir, &heur, &alpha,
+                        &beta, &probe, &bps, &t) != 12)
+            continue;
+        if (kind == k.kind && n == k.n && nnz == k.nnz && sym == k.sym && S == k.S) {
+            gbx_desc_init(d);
+            d->direction = dir;
+            d->heuristic = heur;
+            d->alpha = alpha;
+            d->beta = beta;
+            d->pull_probe = probe;
+            d->blocks_per_sm = bps;
+            *ms = t;
+            found = true;  // the last matching line wins
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+static void cache_store(const char* path, const TuneKey& k, const gbx_desc& d, double ms) {
+    if (!path) return;
+    FILE* f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%d %d %lld %d %d %d %d %.9g %.9g %d %d %.6f\n", k.kind, k.n, k.nnz, k.sym, k.S, d.direction,
+                 d.heuristic, d.alpha, d.beta, d.pull_probe, d.blocks_per_sm, ms);
+    std::fclose(f);
+}
+
+}  // namespace gbx
+
+using namespace gbx;
+
+extern "C" gbx_status gbx_autotune(gbx_graph* g, int32_t kind, const int32_t* sources, int32_t count, gbx_desc* best,
+                                   double* best_ms, const char* cache_path, void* stream) {
+    clear_error();
+    GBX_TRY(check_graph(g));
+    GBX_CHECK(kind == GBX_TUNE_BFS || kind == GBX_TUNE_BATCH, GBX_ERR_INVALID_VALUE, "unknown tuning kind");
+    GBX_CHECK(count >= 1 && sources != nullptr && best != nullptr, GBX_ERR_NULL_POINTER,
+              "sources and best are required, count >= 1");
+    Graph* G = as_impl(g);
+    for (int32_t k = 0; k < count; ++k)
+        GBX_CHECK(sources[k] >= 0 && sources[k] < G->n, GBX_ERR_INVALID_INDEX, "source outside [0, n)");
+    const TuneKey key{kind, G->n, G->symmetric, kind == GBX_TUNE_BATCH ? count : 0, (long long)G->nnz};
+    double cached = 0.0;
+    if (cache_lookup(cache_path, key, best, &cached)) {
+        if (best_ms) *best_ms = cached;
+        return GBX_OK;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    // candidate descriptors
+    std::vector<gbx_desc> cand;
+    gbx_desc base;
+    gbx_desc_init(&base);
+    if (kind == GBX_TUNE_BFS) {
+        const float ratio_a[] = {0.002f, 0.005f, 0.01f, 0.02f, 0.05f, 0.1f};
+        const float beamer_a[] = {1.0f / 64, 1.0f / 32, 1.0f / 16, 1.0f / 14, 1.0f / 8, 1.0f / 4};
+        const float betas[] = {0.01f, 0.05f};
+        for (float b : betas) {
+            for (float a : ratio_a) {
+                gbx_desc d = base;
+                d.heuristic = GBX_HEUR_RATIO;
+                d.alpha = a;
+                d.beta = b;
+                cand.push_back(d);
+            }
+            for (float a : beamer_a) {
+                gbx_desc d = base;
+                d.heuristic = GBX_HEUR_BEAMER;
+                d.alpha = a;
+                d.beta = b;
+                cand.push_back(d);
+            }
+        }
+    } else {
+        const float alphas[] = {0.002f, 0.005f, 0.01f, 0.02f, 0.05f, 0.1f, 0.2f, 0.5f, 1e30f};
+        for (float a : alphas) {
+            gbx_desc d = base;
+            d.alpha = a;
+            cand.push_back(d);
+        }
+    }
+    // buffers
+    void* depth = nullptr;
+    const size_t bytes = kind == GBX_TUNE_BFS ? sizeof(int32_t) * (size_t)G->n
+                                              : sizeof(int16_t) * (size_t)G->n * (size_t)count;
+    GBX_CUDA_TRY(cudaMallocAsync(&depth, bytes, s));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    gbx_status st = GBX_OK;
+    auto run_once = [&](const gbx_desc& d) -> gbx_status {
+        if (kind == GBX_TUNE_BFS) {
+            for (int32_t k = 0; k < count; ++k)
+                GBX_TRY(gbx_bfs(g, sources[k], static_cast<int32_t*>(depth), nullptr, &d, stream));
+            return GBX_OK;
+        }
+        return gbx_bfs_batch(g, sources, count, depth, GBX_DEPTH_I16, &d, stream);
+    };
+    auto time_desc = [&](const gbx_desc& d, double* ms) -> gbx_status {
+        GBX_TRY(run_once(d));  // warm-up
+        GBX_CUDA_TRY(cudaEventRecord(e0, s));
+        GBX_TRY(run_once(d));
+        GBX_CUDA_TRY(cudaEventRecord(e1, s));
+        GBX_CUDA_TRY(cudaEventSynchronize(e1));
+        float t = 0.0f;
+        GBX_CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+        GBX_TRY(gbx_graph_sync(g, stream));
+        *ms = t;
+        return GBX_OK;
+    };
+    cudaError_t ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        st = GBX_ERR_CUDA;
+        set_error(std::string("cudaEventCreate: ") + cudaGetErrorString(ce));
+    }
+    gbx_desc winner = base;
+    double win_ms = 1e300;
+    for (size_t c = 0; c < cand.size() && st == GBX_OK; ++c) {
+        double ms = 0.0;
+        st = time_desc(cand[c], &ms);
+        if (st == GBX_OK && ms < win_ms) {
+            win_ms = ms;
+            winner = cand[c];
+        }
+    }
+    // second stage: lane probe depth and persistent blocks per SM on the winning rule
+    const int32_t probes_bfs[] = {8, 32};
+    const int32_t probes_batch[] = {4, 16};
+    const int32_t* probes = kind == GBX_TUNE_BFS ? probes_bfs : probes_batch;
+    for (int i = 0; i < 2 && st == GBX_OK; ++i) {
+        gbx_desc d = winner;
+        d.pull_probe = probes[i];
+        double ms = 0.0;
+        st = time_desc(d, &ms);
+        if (st == GBX_OK && ms < win_ms) {
+            win_ms = ms;
+            winner = d;
+        }
+    }
+    if (kind == GBX_TUNE_BFS && st == GBX_OK && G->bfs_blocks > 1) {
+        gbx_desc d = winner;
+        d.blocks_per_sm = G->bfs_blocks - 1;
+        double ms = 0.0;
+        st = time_desc(d, &ms);
+        if (st == GBX_OK && ms < win_ms) {
+            win_ms = ms;
+            winner = d;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFreeAsync(depth, s);
+    if (st != GBX_OK) return st;
+    GBX_CUDA_TRY(cudaStreamSynchronize(s));
+    *best = winner;
+    if (best_ms) *best_ms = win_ms;
+    cache_store(cache_path, key, winner, win_ms);
+    return GBX_OK;
+}

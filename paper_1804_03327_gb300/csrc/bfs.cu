@@ -38,7 +38,7 @@ namespace gbx {
 #endif
 constexpr int kBfsThreads = GBX_BFS_THREADS;
 constexpr int kBfsMinBlocks = GBX_BFS_MIN_BLOCKS;
-constexpr int kProbe = GBX_PULL_PROBE;  // in-neighbours one lane examines before the warp takes over the row
+constexpr int kProbe = GBX_PULL_PROBE;  // default in-neighbours a lane examines before the warp takes the row
 enum { DIR_PUSH = GBX_DIR_PUSH, DIR_PULL = GBX_DIR_PULL };
 
 struct BfsArgs {
@@ -62,7 +62,7 @@ struct BfsArgs {
     LevelRec* trace;
     int32_t* status;
     float alpha, beta;
-    int32_t heuristic, mode, early_exit, masking, operand_reuse, symmetric, need_indeg, trace_cap;
+    int32_t heuristic, mode, early_exit, masking, operand_reuse, symmetric, need_indeg, trace_cap, probe;
     unsigned long long timeout_ns;
     unsigned int bar_parity;
 };
@@ -146,7 +146,7 @@ constexpr int kPullIlp = 2;  // candidate rows per lane per round (independent p
 // A warp takes a tile of 32 bitmap words (1024 vertices), finds the rows the
 // mask lets through (unvisited, with in-edges), packs them in registers
 // (per-word popcount, warp scan, __fns) and processes them 64 per round, two
-// rows per lane probing in lockstep; rows longer than kProbe are finished by
+// rows per lane probing in lockstep; rows longer than the probe depth are finished by
 // the whole warp.
 __device__ __forceinline__ void pull_level(const BfsArgs& a, int32_t L, int vcur, bool use_fbm, bool append,
                                            Stage& st, uint32_t* snew, Acc& acc) {
@@ -218,14 +218,14 @@ __device__ __forceinline__ void pull_level(const BfsArgs& a, int32_t L, int vcur
                     }
                 }
             }
-            // lane probes: up to kProbe in-neighbours per row, four at a time, both rows in lockstep
-            for (int it = 0; it < kProbe / 4; ++it) {
+            // lane probes: up to a.probe in-neighbours per row, four at a time, both rows in lockstep
+            for (int it = 0; it < a.probe / 4; ++it) {
                 int32_t jj[kPullIlp][4];
                 int32_t cnt[kPullIlp];
                 bool act[kPullIlp];
 #pragma unroll
                 for (int r = 0; r < kPullIlp; ++r) {
-                    const int32_t lim = end[r] < beg[r] + kProbe ? end[r] : beg[r] + kProbe;
+                    const int32_t lim = end[r] < beg[r] + a.probe ? end[r] : beg[r] + a.probe;
                     act[r] = mine[r] && !done[r] && k[r] < lim;
                     cnt[r] = act[r] ? (lim - k[r] < 4 ? lim - k[r] : 4) : 0;
 #pragma unroll
@@ -519,18 +519,21 @@ static gbx_status check_desc(const gbx_desc* d) {
               "desc.heuristic");
     GBX_CHECK(d->alpha >= 0.0f && d->beta >= 0.0f && d->alpha == d->alpha && d->beta == d->beta,
               GBX_ERR_INVALID_VALUE, "desc.alpha / desc.beta must be >= 0");
-    for (int k = 0; k < 5; ++k) GBX_CHECK(d->reserved[k] == 0, GBX_ERR_INVALID_VALUE, "desc.reserved must be 0");
+    GBX_CHECK(d->pull_probe == 0 || (d->pull_probe >= 4 && d->pull_probe <= 1024), GBX_ERR_INVALID_VALUE,
+              "desc.pull_probe must be 0 or in [4, 1024]");
+    GBX_CHECK(d->blocks_per_sm >= 0, GBX_ERR_INVALID_VALUE, "desc.blocks_per_sm must be >= 0");
+    for (int k = 0; k < 3; ++k) GBX_CHECK(d->reserved[k] == 0, GBX_ERR_INVALID_VALUE, "desc.reserved must be 0");
     return GBX_OK;
 }
 
 static gbx_status bfs_geometry(Graph* G) {
-    if (G->bfs_blocks > 0) return GBX_OK;
+    if (G->bfs_blocks > 0) return GBX_OK;  // blocks per SM that fit (cached per graph)
     int b0 = 0, b1 = 0;
     GBX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, bfs_kernel<false>, kBfsThreads, 0));
     GBX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, bfs_kernel<true>, kBfsThreads, 0));
     const int per_sm = b0 < b1 ? b0 : b1;
     GBX_CHECK(per_sm >= 1, GBX_ERR_CUDA, "BFS kernel cannot be resident");
-    G->bfs_blocks = per_sm * G->num_sms;
+    G->bfs_blocks = per_sm;
     return GBX_OK;
 }
 
@@ -572,11 +575,13 @@ static gbx_status launch_bfs(Graph* G, int32_t source, int32_t* depth, int32_t* 
     a.symmetric = G->symmetric;
     a.need_indeg = (!G->symmetric && (d.trace || d.heuristic == GBX_HEUR_BEAMER)) ? 1 : 0;
     a.trace_cap = kTraceCap;
+    a.probe = d.pull_probe > 0 ? (d.pull_probe + 3) / 4 * 4 : kProbe;
     a.timeout_ns = wait_timeout_ns();
     a.bar_parity = G->ws.bar_parity;
     void* args[] = {&a};
     const void* fn = d.trace ? (const void*)bfs_kernel<true> : (const void*)bfs_kernel<false>;
-    GBX_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(G->bfs_blocks), dim3(kBfsThreads), args, 0, s));
+    const int per_sm = d.blocks_per_sm > 0 && d.blocks_per_sm < G->bfs_blocks ? d.blocks_per_sm : G->bfs_blocks;
+    GBX_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(per_sm * G->num_sms), dim3(kBfsThreads), args, 0, s));
     G->ws.bar_parity ^= 1u;
     G->ws.last_stream = s;
     G->ws.last_traced = d.trace ? 1 : 0;

@@ -24,7 +24,7 @@
 namespace gbx {
 
 constexpr int kMsThreads = 512;
-constexpr int kMsProbe = 8;  // in-neighbours a lane scans alone before the warp takes over
+constexpr int kMsProbe = 8;  // default in-neighbours a lane scans alone before the warp takes over
 
 struct MsArgs {
     int32_t n, S, W, nwords;
@@ -53,7 +53,7 @@ struct MsArgs {
     LevelRec* trace;
     int32_t* status;
     float alpha;
-    int32_t mode, trace_cap, symmetric;
+    int32_t mode, trace_cap, symmetric, probe;
     unsigned long long timeout_ns;
 };
 
@@ -133,10 +133,10 @@ __device__ __forceinline__ void ms_pull(const MsArgs& a, int32_t L, Stage& st, A
                 pend |= unv[j] != 0ull;
             }
             unsigned long long exam = 0;
-            // lane probes: up to kMsProbe in-neighbours, two loads in flight
+            // lane probes: up to a.probe in-neighbours, two loads in flight
             int32_t k = beg;
             bool covered = !pend;
-            const int32_t lim = end < beg + kMsProbe ? end : beg + kMsProbe;
+            const int32_t lim = end < beg + a.probe ? end : beg + a.probe;
             while (!covered && k < lim) {
                 const bool two = k + 1 < lim;
                 const int32_t u0 = __ldg(a.in_col + k);
@@ -575,6 +575,7 @@ gbx_status ms_run(Graph* G, Workspace& w, int32_t S, const int32_t* src_dev, voi
     a.mode = d.direction;
     a.symmetric = G->symmetric;
     a.trace_cap = kTraceCap;
+    a.probe = d.pull_probe > 0 ? d.pull_probe : kMsProbe;
     a.timeout_ns = wait_timeout_ns();
     const gbx_status st = cw == 4 ? ms_launch<4>(G, a, blocks, s)
                                   : (cw == 2 ? ms_launch<2>(G, a, blocks, s) : ms_launch<1>(G, a, blocks, s));
@@ -606,6 +607,8 @@ extern "C" gbx_status gbx_bfs_batch(gbx_graph* g, const int32_t* sources, int32_
         gbx_desc_init(&d);
     GBX_CHECK(d.direction >= GBX_DIR_AUTO && d.direction <= GBX_DIR_PULL, GBX_ERR_INVALID_VALUE, "desc.direction");
     GBX_CHECK(d.alpha >= 0.0f && d.alpha == d.alpha, GBX_ERR_INVALID_VALUE, "desc.alpha must be >= 0");
+    GBX_CHECK(d.pull_probe == 0 || (d.pull_probe >= 4 && d.pull_probe <= 1024), GBX_ERR_INVALID_VALUE,
+              "desc.pull_probe must be 0 or in [4, 1024]");
     cudaStream_t s = (cudaStream_t)stream;
     GBX_TRY(ms_reserve(G->ws, G->n, S, s));
     if (G->ws.ms_src_cap < S) {

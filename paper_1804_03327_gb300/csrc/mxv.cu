@@ -228,7 +228,7 @@ extern "C" gbx_status gbx_mxv(gbx_vector* w, const gbx_vector* mask, int32_t sem
         gbx_desc_init(&d);
     GBX_CHECK(d.direction >= GBX_DIR_AUTO && d.direction <= GBX_DIR_PULL, GBX_ERR_INVALID_VALUE, "desc.direction");
     GBX_CHECK(d.alpha >= 0.0f && d.alpha == d.alpha, GBX_ERR_INVALID_VALUE, "desc.alpha must be >= 0");
-    for (int k = 0; k < 5; ++k) GBX_CHECK(d.reserved[k] == 0, GBX_ERR_INVALID_VALUE, "desc.reserved must be 0");
+    for (int k = 0; k < 3; ++k) GBX_CHECK(d.reserved[k] == 0, GBX_ERR_INVALID_VALUE, "desc.reserved must be 0");
     cudaStream_t s = (cudaStream_t)stream;
 
     // w = A' u with A' = A^T (transpose) or A.  Pull reads rows of A' (CSR of A'),

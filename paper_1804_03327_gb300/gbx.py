@@ -45,6 +45,8 @@ HEUR_BEAMER = 1
 LOR_LAND = 0
 DEPTH_I32 = 0
 DEPTH_I16 = 1
+TUNE_BFS = 0
+TUNE_BATCH = 1
 
 EXPORTED = [
     "gbx_last_error", "gbx_status_string", "gbx_version", "gbx_graph_build", "gbx_graph_free", "gbx_graph_info",
@@ -52,7 +54,7 @@ EXPORTED = [
     "gbx_bfs", "gbx_bfs_host", "gbx_bfs_trace", "gbx_set_wait_timeout_ns", "gbx_selftest_barrier_timeout",
     "gbx_mxv_pull_noalloc", "gbx_bfs_batch", "gbx_bfs_batch_trace",
     "gbx_server_config_init", "gbx_server_create", "gbx_server_add_graph", "gbx_server_graph_lanes",
-    "gbx_server_submit", "gbx_server_poll", "gbx_server_stats", "gbx_server_destroy",
+    "gbx_server_submit", "gbx_server_poll", "gbx_server_stats", "gbx_server_destroy", "gbx_autotune",
 ]
 
 
@@ -71,7 +73,8 @@ class Desc(ctypes.Structure):
     _fields_ = [("transpose", ctypes.c_int32), ("mask_complement", ctypes.c_int32), ("early_exit", ctypes.c_int32),
                 ("accum", ctypes.c_int32), ("direction", ctypes.c_int32), ("heuristic", ctypes.c_int32),
                 ("alpha", ctypes.c_float), ("beta", ctypes.c_float), ("masking", ctypes.c_int32),
-                ("operand_reuse", ctypes.c_int32), ("trace", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("operand_reuse", ctypes.c_int32), ("trace", ctypes.c_int32), ("pull_probe", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class Level(ctypes.Structure):
@@ -143,6 +146,8 @@ def load():
                 "gbx_server_stats": (ctypes.c_int, [p, ctypes.POINTER(i64), ctypes.POINTER(i32),
                                                     ctypes.POINTER(i64), ctypes.POINTER(i64)]),
                 "gbx_server_destroy": (ctypes.c_int, [p]),
+                "gbx_autotune": (ctypes.c_int, [p, i32, p, i32, ctypes.POINTER(Desc), ctypes.POINTER(ctypes.c_double),
+                                                ctypes.c_char_p, p]),
             }
             for name, (res, args) in sigs.items():
                 fn = getattr(L, name)
@@ -328,6 +333,20 @@ def bfs_host(g: Graph, sources, depth_host: np.ndarray, parent_host: np.ndarray 
     st = load().gbx_bfs_host(g.handle, srcs.ctypes.data, len(srcs), dptr, pptr,
                              ctypes.byref(desc) if desc is not None else None, _stream_ptr(stream))
     _check(st, "gbx_bfs_host")
+
+
+def autotune(g: Graph, kind: int, sources, cache_path: str | None = None, stream=None):
+    """Fastest descriptor for g on these sources: (Desc, ms)."""
+    srcs = np.ascontiguousarray(sources, dtype=np.int32)
+    d = Desc()
+    ms = ctypes.c_double()
+    _check(load().gbx_autotune(g.handle, int(kind), srcs.ctypes.data, len(srcs), ctypes.byref(d), ctypes.byref(ms),
+                               cache_path.encode() if cache_path else None, _stream_ptr(stream)), "gbx_autotune")
+    return d, ms.value
+
+
+def desc_dict(d: Desc) -> dict:
+    return {f: (list(getattr(d, f)) if f == "reserved" else getattr(d, f)) for f, _ in d._fields_ if f != "reserved"}
 
 
 def bfs_batch(g: Graph, sources, depth, desc: Desc | None = None, stream=None):
