@@ -57,6 +57,8 @@ def parse():
     p.add_argument("--no-served", action="store_true", help="skip the serving measurement")
     p.add_argument("--serve-seconds", type=float, default=2.0)
     p.add_argument("--serve-rate", type=float, default=20000.0)
+    p.add_argument("--sweep", action="store_true",
+                   help="masked-mxv operator sweep (RMAT scale 20 and the 2048x2048 grid) instead of the BFS line")
     p.add_argument("--probe", type=int, default=None, metavar="K",
                    help="profiling aid: run only source K of the workload --repeat times (for ncu -k bfs_kernel)")
     p.add_argument("--repeat", type=int, default=5)
@@ -210,6 +212,82 @@ def cpu_oracle_baseline(n, src, dst, sources, sample: int):
     for d in depths:
         edges += int(deg[d >= 0].sum()) // 2
     return edges / dt / 1e9, dt, edges
+
+
+def run_sweep(args):
+    """Masked matvec operator sweep (the Figure 2 / Figure 6 microbenchmark on
+    synthetic graphs): w = A^T u .* !m for random u (frontier) and m (visited)
+    of given densities, in each direction, dense-uint8 or sparse-int32 u.
+    Bytes per call = algorithmic bytes from the call's own work counters:
+    push 12 B per frontier entry + 4 B per expanded edge; pull 8 B per computed
+    row + 4 B per examined entry; plus the vectors (1 B per entry dense, 4 B per
+    index sparse) and the n/8-byte bitmaps each direction streams."""
+    import torch
+
+    import synth
+    from paper_1804_03327_gb300 import gbx
+
+    peak, peak_kind = peaks()
+    fdens = list(np.logspace(-5, np.log10(0.5), 12))
+    mdens = list(np.logspace(-2, np.log10(0.99), 9))
+    out = {"metric": "masked mxv time and achieved GB/s", "unit": "GB/s", "peak": peak, "peak_kind": peak_kind,
+           "frontier_density": fdens, "unvisited_density": mdens, "graphs": {}}
+    for name, gen in [("rmat20-ef16", lambda: synth.rmat_edges(20, EDGE_FACTOR, seed=SEED)),
+                      ("grid2048-del1pct", lambda: synth.grid_edges(2048, 2048, 0.01, seed=SEED))]:
+        n, src, dst = gen()
+        g = gbx.graph_build(n, src, dst)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        w = torch.zeros(n, dtype=torch.uint8, device="cuda")
+        res = []
+        for fi, fd in enumerate(fdens):
+            u8 = torch.from_numpy(synth.vertex_set(n, fd, seed=SEED, stream=fi)).cuda()
+            idx = torch.nonzero(u8).flatten().to(torch.int32)
+            ulist = torch.zeros(n, dtype=torch.int32, device="cuda")
+            ulist[: idx.numel()] = idx
+            ucnt = torch.tensor([idx.numel()], dtype=torch.int32, device="cuda")
+            for mi, md in enumerate(mdens):
+                # unvisited density md: the mask is the visited set (complemented, as in BFS)
+                vis = torch.from_numpy(synth.vertex_set(n, 1.0 - md, seed=SEED + 1, stream=mi)).cuda()
+                row = {"f": fd, "m_unvisited": md}
+                variants = [("push", gbx.DIR_PUSH, 1, True), ("pull", gbx.DIR_PULL, 0, True),
+                            ("pull_early_exit", gbx.DIR_PULL, 1, True)]
+                if mi == 0:
+                    variants.append(("pull_unmasked", gbx.DIR_PULL, 0, False))  # Eq 2: no mask
+                for label, direction, ee, masked in variants:
+                    for fmt in ("dense_u8", "sparse_i32"):
+                        uvec = gbx.dense(u8) if fmt == "dense_u8" else gbx.sparse(ulist, ucnt, n)
+                        desc = gbx.desc_init(direction=direction, early_exit=ee, mask_complement=int(masked), trace=1)
+                        mvec = gbx.dense(vis) if masked else None
+                        gbx.mxv(gbx.dense(w), mvec, gbx.LOR_LAND, g, uvec, desc)
+                        st = gbx.mxv_stats(g)
+                        ts = []
+                        for _ in range(3):
+                            e0.record()
+                            gbx.mxv(gbx.dense(w), mvec, gbx.LOR_LAND, g, uvec, desc)
+                            e1.record()
+                            torch.cuda.synchronize()
+                            ts.append(e0.elapsed_time(e1))
+                        t = float(np.median(ts)) / 1e3
+                        vec = n if fmt == "dense_u8" else 4 * int(idx.numel())
+                        if direction == gbx.DIR_PUSH:
+                            alg = 12 * st["u_nnz"] + 4 * st["edges"] + n // 8 * 2
+                        else:
+                            alg = 8 * st["rows"] + 4 * st["examined"] + n // 8 * 3
+                        alg += vec + (n if masked else 0) + n  # u, the mask (dense bytes), the dense output
+                        row[f"{label}_{fmt}_ms"] = t * 1e3
+                        row[f"{label}_{fmt}_gbs"] = alg / t / 1e9
+                res.append(row)
+        # crossover: smallest frontier density at which pull with early exit beats push (dense u)
+        cross = {}
+        for mi, md in enumerate(mdens):
+            pts = [r for r in res if r["m_unvisited"] == md]
+            xs = [r["f"] for r in pts if r["pull_early_exit_dense_u8_ms"] < r["push_dense_u8_ms"]]
+            cross[f"{md:.3g}"] = min(xs) if xs else None
+        best = max(max(r[k] for k in r if k.endswith("_gbs")) for r in res)
+        out["graphs"][name] = {"points": res, "pull_beats_push_from_frontier_density": cross,
+                               "best_gbs": best, "best_frac": best / peak}
+        g.free()
+    print(json.dumps(out), flush=True)
 
 
 def run_reference(args):
@@ -601,6 +679,8 @@ def main():
     args = parse()
     if args.probe is not None:
         run_probe(args)
+    elif args.sweep:
+        run_sweep(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
