@@ -17,6 +17,9 @@ namespace gbx {
 
 constexpr int kMxvThreads = 256;
 constexpr int kMxvProbe = 16;
+constexpr int kMxvLaneRow = 32;
+constexpr int kMxvHugeRow = 4096;  // rows longer than this are spread over every warp
+constexpr int kMxvChunk = 1024;
 
 // Per-call counters (desc.trace): [0] rows computed by pull, [1] entries
 // examined by pull, [2] nonzeros of u expanded by push, [3] edges expanded.
@@ -26,72 +29,175 @@ struct MxvStats {
 
 __device__ __forceinline__ bool dir_enabled(const int32_t* flag, int want) { return !flag || *flag == want; }
 
+// Row-based matvec over the rows the mask lets through (Eq 2 / Eq 4).  A warp
+// takes a tile of 32 result words (1024 rows), packs the passing nonempty rows
+// in registers (popcount, warp scan, __fns) and computes them 64 per round, two
+// rows per lane probing in lockstep: the first entry of a row comes from the
+// dense first-entry array when one is given (one coalesced read instead of a
+// random sector), then up to kMxvProbe entries four at a time; longer rows are
+// finished by the whole warp 32 entries at a time.  With early exit a row stops
+// at its first hit (Section 5.3); the result is the same either way.
+constexpr int kMxvIlp = 2;
+
 __global__ void __launch_bounds__(kMxvThreads) mxv_pull_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                                                                const int32_t* __restrict__ first,
                                                                 const uint32_t* __restrict__ nzrows,
                                                                 const uint32_t* __restrict__ ubm,
                                                                 const uint32_t* __restrict__ pass, uint32_t* __restrict__ R,
                                                                 int32_t nwords, int early_exit, const int32_t* flag,
-                                                                MxvStats* stats) {
+                                                                MxvStats* stats, int32_t* huge, int32_t* huge_next,
+                                                                int32_t* huge_count) {
     if (!dir_enabled(flag, GBX_DIR_PULL)) return;
+    __shared__ uint32_t tile_hits[kMxvThreads / 32][32];
+    uint32_t* hits = tile_hits[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+    const int32_t ntiles = (nwords + 31) >> 5;
     unsigned long long rows = 0, exam = 0;
-    for (int32_t w = gwarp; w < nwords; w += nwarps) {
-        const uint32_t cand = (pass ? pass[w] : 0xffffffffu) & nzrows[w];
-        if (cand == 0) {
-            if (lane == 0) R[w] = 0u;
-            continue;
-        }
-        const int32_t i = (w << 5) + lane;
-        const bool mine = (cand >> lane) & 1u;
-        int32_t k = 0, end = 0;
-        bool found = false, done = false;
-        if (mine) {
-            rows += 1;
-            k = ptr[i];
-            end = ptr[i + 1];
-            const int32_t lim = end < k + kMxvProbe ? end : k + kMxvProbe;
-            while (k < lim) {
-                const bool h = bit_test(ubm, col[k]);
+    for (int32_t tile = gwarp; tile < ntiles; tile += nwarps) {
+        const int32_t w = (tile << 5) + lane;
+        const bool wok = w < nwords;
+        const uint32_t cand = wok ? ((pass ? pass[w] : 0xffffffffu) & nzrows[w]) : 0u;
+        const uint32_t cntw = __popc(cand);
+        const uint32_t incl = warp_inclusive_sum(cntw);
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        const uint32_t excl = incl - cntw;
+        hits[lane] = 0u;
+        __syncwarp();
+        for (uint32_t base = 0; base < total; base += 32 * kMxvIlp) {
+            bool mine[kMxvIlp], found[kMxvIlp], done[kMxvIlp];
+            int jw[kMxvIlp], bitpos[kMxvIlp];
+            int32_t k[kMxvIlp], end[kMxvIlp], beg[kMxvIlp], f0[kMxvIlp];
+#pragma unroll
+            for (int r = 0; r < kMxvIlp; ++r) {
+                const uint32_t c = base + 32 * r + lane;
+                mine[r] = c < total;
+                int j = 0;
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1) {
+                    const uint32_t ev = __shfl_sync(0xffffffffu, excl, j + step);
+                    if (ev <= c) j += step;
+                }
+                jw[r] = j;
+                const uint32_t cj = __shfl_sync(0xffffffffu, cand, j);
+                const uint32_t ej = __shfl_sync(0xffffffffu, excl, j);
+                bitpos[r] = mine[r] ? (int)__fns(cj, 0u, (int)(c - ej) + 1) : 0;
+                found[r] = false;
+                done[r] = false;
+            }
+#pragma unroll
+            for (int r = 0; r < kMxvIlp; ++r) {
+                const int32_t i = (((tile << 5) + jw[r]) << 5) + bitpos[r];
+                beg[r] = mine[r] ? ptr[i] : 0;
+                end[r] = mine[r] ? ptr[i + 1] : 0;
+                f0[r] = mine[r] ? (first ? first[i] : -2) : -1;
+            }
+#pragma unroll
+            for (int r = 0; r < kMxvIlp; ++r) {
+                if (!mine[r]) continue;
+                rows += 1;
+                if (f0[r] == -2) f0[r] = col[beg[r]];  // no first-entry array: read the row's first entry
+                k[r] = beg[r] + 1;
                 exam += 1;
-                ++k;
-                if (h) {
-                    found = true;
-                    if (early_exit) {
-                        done = true;
-                        break;
-                    }
+                if (bit_test(ubm, f0[r])) {
+                    found[r] = true;
+                    done[r] = early_exit != 0;
                 }
             }
-        }
-        uint32_t pend = __ballot_sync(0xffffffffu, mine && !done && k < end);
-        while (pend) {
-            const int t = __ffs(pend) - 1;
-            pend &= pend - 1;
-            int32_t kk = __shfl_sync(0xffffffffu, k, t);
-            const int32_t ee = __shfl_sync(0xffffffffu, end, t);
-            bool tf = __shfl_sync(0xffffffffu, found, t);
-            unsigned long long tx = 0;
-            for (; kk < ee; kk += 32) {
-                const int32_t idx = kk + lane;
-                const uint32_t hb = __ballot_sync(0xffffffffu, idx < ee && bit_test(ubm, col[idx]));
-                if (hb) {
-                    tf = true;
-                    if (early_exit) {
-                        tx += (unsigned long long)(__ffs(hb));
-                        break;
+            // a lane scans rows of up to kMxvLaneRow entries itself; longer rows get kMxvProbe
+            // entries here and the rest from the whole warp below
+            while (true) {
+                int32_t jj[kMxvIlp][4];
+                int32_t cnt[kMxvIlp];
+                bool act[kMxvIlp];
+#pragma unroll
+                for (int r = 0; r < kMxvIlp; ++r) {
+                    const int32_t span = end[r] - beg[r] <= kMxvLaneRow ? kMxvLaneRow : kMxvProbe;
+                    const int32_t lim = end[r] < beg[r] + span ? end[r] : beg[r] + span;
+                    act[r] = mine[r] && !done[r] && k[r] < lim;
+                    cnt[r] = act[r] ? (lim - k[r] < 4 ? lim - k[r] : 4) : 0;
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) jj[r][t] = t < cnt[r] ? col[k[r] + t] : 0;
+                }
+                if (!__any_sync(0xffffffffu, act[0] || act[1])) break;
+#pragma unroll
+                for (int r = 0; r < kMxvIlp; ++r) {
+                    if (!act[r]) continue;
+                    int hit = -1;
+#pragma unroll
+                    for (int t = 3; t >= 0; --t)
+                        if (t < cnt[r] && bit_test(ubm, jj[r][t])) hit = t;
+                    if (hit >= 0) {
+                        found[r] = true;
+                        if (early_exit) {
+                            exam += (unsigned long long)(hit + 1);
+                            k[r] += hit + 1;
+                            done[r] = true;
+                            continue;
+                        }
+                    }
+                    exam += (unsigned long long)cnt[r];
+                    k[r] += cnt[r];
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < kMxvIlp; ++r) {
+                if (huge && mine[r] && !done[r] && end[r] - beg[r] > kMxvHugeRow) {
+                    // still unresolved after the lane probe: mxv_pull_huge_kernel scans the rest of
+                    // the row with a whole block (a found row keeps its bit from the probe)
+                    const int32_t i = (((tile << 5) + jw[r]) << 5) + bitpos[r];
+                    const int32_t slot = atomicAdd(huge_count, 1);  // fewer than n rows: fits
+                    huge[slot] = i;
+                    huge_next[slot] = k[r];
+                    done[r] = true;
+                }
+                uint32_t pend = __ballot_sync(0xffffffffu, mine[r] && !done[r] && k[r] < end[r]);
+                while (pend) {
+                    const int t = __ffs(pend) - 1;
+                    pend &= pend - 1;
+                    int32_t kk = __shfl_sync(0xffffffffu, k[r], t);
+                    const int32_t ee = __shfl_sync(0xffffffffu, end[r], t);
+                    bool tf = __shfl_sync(0xffffffffu, found[r], t);
+                    unsigned long long tx = 0;
+                    // 128 entries per round (four independent loads per lane)
+                    for (; kk < ee; kk += 128) {
+                        int32_t jq[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int32_t idx = kk + 32 * q + lane;
+                            jq[q] = idx < ee ? col[idx] : -1;
+                        }
+                        bool stop = false;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            if (stop) break;
+                            const uint32_t hb = __ballot_sync(0xffffffffu, jq[q] >= 0 && bit_test(ubm, jq[q]));
+                            const int32_t left = ee - (kk + 32 * q);
+                            if (left <= 0) break;
+                            if (hb) {
+                                tf = true;
+                                if (early_exit) {
+                                    tx += (unsigned long long)__ffs(hb);
+                                    stop = true;
+                                    break;
+                                }
+                            }
+                            tx += (unsigned long long)(left < 32 ? left : 32);
+                        }
+                        if (stop) break;
+                    }
+                    if (lane == t) {
+                        found[r] = tf;
+                        exam += tx;
                     }
                 }
-                tx += (unsigned long long)(ee - kk < 32 ? ee - kk : 32);
-            }
-            if (lane == t) {
-                found = tf;
-                exam += tx;
+                if (found[r]) atomicOr(hits + jw[r], 1u << bitpos[r]);
             }
         }
-        const uint32_t fm = __ballot_sync(0xffffffffu, found);
-        if (lane == 0) R[w] = fm;
+        __syncwarp();
+        if (wok) R[w] = hits[lane];
+        __syncwarp();
     }
     if (stats) {
         rows = warp_sum_u64(rows);
@@ -100,6 +206,44 @@ __global__ void __launch_bounds__(kMxvThreads) mxv_pull_kernel(const int32_t* __
             if (rows) atomicAdd(&stats->rows, rows);
             if (exam) atomicAdd(&stats->exam, exam);
         }
+    }
+}
+
+// Rows longer than kMxvHugeRow that the lane probe left unresolved: block b takes
+// rows b, b + gridDim.x, ... of the deferred list (row, next entry) and its warps
+// split the rest of the row into 1024-entry chunks, so a power-law hub is not
+// scanned by one warp.  A hit sets the row's result bit; with early exit, chunks
+// of a row already found are skipped.
+__global__ void __launch_bounds__(kMxvThreads) mxv_pull_huge_kernel(const int32_t* __restrict__ ptr,
+                                                                     const int32_t* __restrict__ col,
+                                                                     const uint32_t* __restrict__ ubm, uint32_t* R,
+                                                                     const int32_t* huge, const int32_t* huge_next,
+                                                                     const int32_t* huge_count,
+                                                                     int early_exit, const int32_t* flag, MxvStats* stats) {
+    if (!dir_enabled(flag, GBX_DIR_PULL)) return;
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    const int32_t count = *huge_count;
+    unsigned long long exam = 0;
+    for (int32_t h = blockIdx.x; h < count; h += gridDim.x) {
+        const int32_t i = huge[h];
+        const int32_t beg = huge_next[h], end = ptr[i + 1];
+        for (int32_t c0 = beg + wib * kMxvChunk; c0 < end; c0 += nw * kMxvChunk) {
+            if (early_exit && ((__ldcg(R + (i >> 5)) >> (i & 31)) & 1u)) break;
+            const int32_t c1 = end - c0 > kMxvChunk ? c0 + kMxvChunk : end;
+            bool hit = false;
+            for (int32_t k = c0 + lane; k < c1; k += 32) hit |= bit_test(ubm, col[k]);
+            exam += (unsigned long long)((c1 - c0) / 32 + (lane < (c1 - c0) % 32 ? 1 : 0));
+            if (__any_sync(0xffffffffu, hit)) {
+                if (lane == 0) atomicOr(R + (i >> 5), 1u << (i & 31));
+                if (early_exit) break;
+            }
+        }
+    }
+    if (stats) {
+        exam = warp_sum_u64(exam);
+        if (lane == 0 && exam) atomicAdd(&stats->exam, exam);
     }
 }
 
@@ -236,6 +380,7 @@ extern "C" gbx_status gbx_mxv(gbx_vector* w, const gbx_vector* mask, int32_t sem
     const int32_t* pull_ptr = d.transpose ? G->in_ptr : G->out_ptr;
     const int32_t* pull_col = d.transpose ? G->in_col : G->out_col;
     const uint32_t* pull_nz = d.transpose ? G->nz_in : G->nz_out;
+    const int32_t* pull_first = d.transpose ? G->first_in : G->first_out;
     const int32_t* push_ptr = d.transpose ? G->out_ptr : G->in_ptr;
     const int32_t* push_col = d.transpose ? G->out_col : G->in_col;
 
@@ -285,7 +430,8 @@ extern "C" gbx_status gbx_mxv(gbx_vector* w, const gbx_vector* mask, int32_t sem
         if (d.mask_complement) GBX_TRY(invert_bitmap(pass, n, s));
         pass_bm = pass;
     }
-    GBX_TRY(fill_bitmap(R, n, 0u, s));
+    // a pull writes every result word; push accumulates into a cleared bitmap
+    if (want_push || nothing_passes) GBX_TRY(fill_bitmap(R, n, 0u, s));
     if (!nothing_passes) {
         const int32_t* flag = nullptr;
         if (dir == GBX_DIR_AUTO) {
@@ -302,8 +448,15 @@ extern "C" gbx_status gbx_mxv(gbx_vector* w, const gbx_vector* mask, int32_t sem
                                                                     ulist, ucount, n, pre, pass_bm, R, flag, stats);
         }
         if (want_pull) {
-            mxv_pull_kernel<<<G->num_sms * 8, kMxvThreads, 0, s>>>(pull_ptr, pull_col, pull_nz, ubm, pass_bm, R,
-                                                                    G->nwords, d.early_exit ? 1 : 0, flag, stats);
+            int32_t* huge = G->ws.q[1];
+            int32_t* huge_next = G->ws.qp[1];
+            int32_t* huge_count = G->ws.flag + 2;
+            GBX_CUDA_TRY(cudaMemsetAsync(huge_count, 0, sizeof(int32_t), s));
+            mxv_pull_kernel<<<G->num_sms * 8, kMxvThreads, 0, s>>>(pull_ptr, pull_col, pull_first, pull_nz, ubm,
+                                                                    pass_bm, R, G->nwords, d.early_exit ? 1 : 0, flag,
+                                                                    stats, huge, huge_next, huge_count);
+            mxv_pull_huge_kernel<<<G->num_sms * 8, kMxvThreads, 0, s>>>(pull_ptr, pull_col, ubm, R, huge, huge_next,
+                                                                         huge_count, d.early_exit ? 1 : 0, flag, stats);
         }
     }
     // output

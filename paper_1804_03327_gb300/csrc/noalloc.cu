@@ -28,9 +28,10 @@ static int g_noalloc_sms[kNoAllocMaxDevices] = {};
 
 // The row-based masked matvec kernel of gbx_mxv (mxv.cu).
 struct MxvStats;
-__global__ void mxv_pull_kernel(const int32_t* ptr, const int32_t* col, const uint32_t* nzrows, const uint32_t* ubm,
-                                const uint32_t* pass, uint32_t* R, int32_t nwords, int early_exit, const int32_t* flag,
-                                MxvStats* stats);
+__global__ void mxv_pull_kernel(const int32_t* ptr, const int32_t* col, const int32_t* first, const uint32_t* nzrows,
+                                const uint32_t* ubm, const uint32_t* pass, uint32_t* R, int32_t nwords, int early_exit,
+                                const int32_t* flag, MxvStats* stats, int32_t* huge, int32_t* huge_next,
+                                int32_t* huge_count);
 
 __global__ void noalloc_nonempty_rows_kernel(const int32_t* __restrict__ row_ptr, int32_t n, uint32_t* __restrict__ bm) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -95,8 +96,8 @@ extern "C" gbx_status gbx_mxv_pull_noalloc(int32_t n, const int32_t* row_ptr, co
         if (mask) GBX_TRY(pack_dense_to_bitmap(mask, n, mask_complement ? 1u : 0u, pass, s));
         const int64_t nw32 = ((int64_t)n + 31) & ~(int64_t)31;
         noalloc_nonempty_rows_kernel<<<div_up(nw32, 256), 256, 0, s>>>(row_ptr, n, nzrows);
-        mxv_pull_kernel<<<sms * 8, 256, 0, s>>>(row_ptr, col, nzrows, ubm, mask ? pass : nullptr, R, nwords,
-                                                early_exit ? 1 : 0, nullptr, nullptr);
+        mxv_pull_kernel<<<sms * 8, 256, 0, s>>>(row_ptr, col, nullptr, nzrows, ubm, mask ? pass : nullptr, R, nwords,
+                                                early_exit ? 1 : 0, nullptr, nullptr, nullptr, nullptr, nullptr);
     }
     GBX_TRY(bitmap_to_dense(R, n, nullptr, w, s));
     GBX_CUDA_TRY(cudaGetLastError());

@@ -205,18 +205,36 @@ __device__ __forceinline__ uint32_t tail_mask(int32_t n, int32_t w) {
     return rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
 }
 
+// One thread per bitmap word: reads the word's 32 bytes (two 16-byte loads when
+// the vector is 16-byte aligned), writes the word.
 __global__ void pack_dense_kernel(const uint8_t* __restrict__ dense, int32_t n, uint32_t invert, uint32_t* __restrict__ bm) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t nw32 = ((int64_t)n + 31) & ~(int64_t)31;
-    if (i - (threadIdx.x & 31) >= nw32) return;
-    const bool set = i < n && (((dense[i] != 0) ? 1u : 0u) ^ invert);
-    const uint32_t word = __ballot_sync(0xffffffffu, set);
-    if ((threadIdx.x & 31) == 0 && i < nw32) bm[i >> 5] = word;
+    const int32_t nw = (n + 31) >> 5;
+    const bool vec = (reinterpret_cast<uintptr_t>(dense) & 15u) == 0;
+    for (int32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += gridDim.x * blockDim.x) {
+        const int64_t base = (int64_t)w << 5;
+        uint32_t word = 0;
+        if (vec && base + 32 <= n) {
+            const uint4 a = reinterpret_cast<const uint4*>(dense + base)[0];
+            const uint4 b = reinterpret_cast<const uint4*>(dense + base)[1];
+            const uint32_t v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+#pragma unroll
+                for (int t = 0; t < 4; ++t) word |= (((v[q] >> (8 * t)) & 0xffu) != 0u ? 1u : 0u) << (4 * q + t);
+        } else {
+            for (int t = 0; t < 32 && base + t < n; ++t) word |= (dense[base + t] != 0 ? 1u : 0u) << t;
+        }
+        if (invert) {
+            const int64_t rem = n - base;
+            word = ~word & (rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u));
+        }
+        bm[w] = word;
+    }
 }
 
 gbx_status pack_dense_to_bitmap(const uint8_t* dense, int32_t n, uint32_t invert, uint32_t* bm, cudaStream_t s) {
-    const int64_t tot = ((int64_t)n + 31) & ~(int64_t)31;
-    pack_dense_kernel<<<div_up(tot, 256), 256, 0, s>>>(dense, n, invert ? 1u : 0u, bm);
+    const int32_t nw = (n + 31) >> 5;
+    pack_dense_kernel<<<max(1u, min(div_up(nw, 256), 152u * 16)), 256, 0, s>>>(dense, n, invert ? 1u : 0u, bm);
     GBX_CUDA_TRY(cudaGetLastError());
     return GBX_OK;
 }
@@ -294,17 +312,49 @@ gbx_status bitmap_to_list(const uint32_t* bm, int32_t n, int32_t* list, int32_t*
     return GBX_OK;
 }
 
+// One thread per bitmap word: writes the word's 32 bytes (two 16-byte stores when
+// aligned), OR-ing in the old dense value when accumulating.
 __global__ void bitmap_to_dense_kernel(const uint32_t* __restrict__ bm, int32_t n, const uint8_t* old_dense,
                                        uint8_t* out) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    uint8_t v = (uint8_t)((bm[i >> 5] >> (i & 31)) & 1u);
-    if (old_dense) v |= (old_dense[i] != 0) ? 1 : 0;
-    out[i] = v;
+    const int32_t nw = (n + 31) >> 5;
+    const bool vec = (reinterpret_cast<uintptr_t>(out) & 15u) == 0 &&
+                     (old_dense == nullptr || (reinterpret_cast<uintptr_t>(old_dense) & 15u) == 0);
+    for (int32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += gridDim.x * blockDim.x) {
+        const uint32_t word = bm[w];
+        const int64_t base = (int64_t)w << 5;
+        if (vec && base + 32 <= n) {
+            uint32_t v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                uint32_t x = 0;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) x |= ((word >> (4 * q + t)) & 1u) << (8 * t);
+                v[q] = x;
+            }
+            if (old_dense) {
+                const uint4 a = reinterpret_cast<const uint4*>(old_dense + base)[0];
+                const uint4 b = reinterpret_cast<const uint4*>(old_dense + base)[1];
+                const uint32_t o[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) v[q] |= (((o[q] >> (8 * t)) & 0xffu) != 0u ? 1u : 0u) << (8 * t);
+            }
+            reinterpret_cast<uint4*>(out + base)[0] = make_uint4(v[0], v[1], v[2], v[3]);
+            reinterpret_cast<uint4*>(out + base)[1] = make_uint4(v[4], v[5], v[6], v[7]);
+        } else {
+            for (int t = 0; t < 32 && base + t < n; ++t) {
+                uint8_t x = (uint8_t)((word >> t) & 1u);
+                if (old_dense) x |= old_dense[base + t] != 0 ? 1 : 0;
+                out[base + t] = x;
+            }
+        }
+    }
 }
 
 gbx_status bitmap_to_dense(const uint32_t* bm, int32_t n, const uint8_t* old_dense, uint8_t* out, cudaStream_t s) {
-    bitmap_to_dense_kernel<<<div_up(n, 256), 256, 0, s>>>(bm, n, old_dense, out);
+    const int32_t nw = (n + 31) >> 5;
+    bitmap_to_dense_kernel<<<max(1u, min(div_up(nw, 256), 152u * 16)), 256, 0, s>>>(bm, n, old_dense, out);
     GBX_CUDA_TRY(cudaGetLastError());
     return GBX_OK;
 }
