@@ -59,6 +59,8 @@ def parse():
     p.add_argument("--serve-rate", type=float, default=20000.0)
     p.add_argument("--sweep", action="store_true",
                    help="masked-mxv operator sweep (RMAT scale 20 and the 2048x2048 grid) instead of the BFS line")
+    p.add_argument("--ablation", action="store_true",
+                   help="Table 2 ladder and per-level push/pull costs on RMAT scale 21 (edge factor 48)")
     p.add_argument("--probe", type=int, default=None, metavar="K",
                    help="profiling aid: run only source K of the workload --repeat times (for ncu -k bfs_kernel)")
     p.add_argument("--repeat", type=int, default=5)
@@ -288,6 +290,90 @@ def run_sweep(args):
                                "best_gbs": best, "best_frac": best / peak}
         g.free()
     print(json.dumps(out), flush=True)
+
+
+def run_ablation(args):
+    """Table 2's cumulative optimisations and the per-level push/pull costs of
+    Figures 5-6, on RMAT scale 21 with edge factor 48 (181M stored edges, the
+    size of the paper's kron_g500-logn21; the dataset itself is not available).
+    Structure-only (Section 5.5) is always on: the library stores no values.
+    Each BFS level starts from the same state whatever the direction (depths do
+    not depend on it), so push-only and pull-only traced runs give every level's
+    cost in both directions, and their per-level minimum is the best schedule a
+    direction rule could pick (the comparison Section 6.3 tunes alpha against)."""
+    import torch
+
+    import synth
+    from paper_1804_03327_gb300 import gbx, roofline
+
+    n, src, dst = synth.rmat_edges(21, 48, seed=SEED)
+    g = gbx.graph_build(n, src, dst)
+    _, nnz, _ = g.info()
+    srcs = synth.sources(n, src, dst, 16, seed=SEED)
+    depth = torch.empty(n, dtype=torch.int32, device="cuda")
+    parent = torch.empty(n, dtype=torch.int32, device="cuda")
+    reached = []
+    for s0 in srcs:
+        gbx.bfs(g, int(s0), depth, parent, gbx.desc_init(trace=1))
+        reached.append(roofline.reached_edges(gbx.bfs_trace(g)))
+
+    def timed(desc, reps=3):
+        for s0 in srcs:
+            gbx.bfs(g, int(s0), depth, parent, desc)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            for s0 in srcs:
+                gbx.bfs(g, int(s0), depth, parent, desc)
+        e1.record()
+        torch.cuda.synchronize()
+        gbx.graph_sync(g)
+        t = e0.elapsed_time(e1) / 1e3 / reps
+        return {"ms_per_bfs": t * 1e3 / len(srcs), "gteps": sum(reached) / t / 1e9}
+
+    ladder = [("push only (structure-only always on)", gbx.desc_init(direction=gbx.DIR_PUSH)),
+              ("+ change of direction", gbx.desc_init(masking=0, early_exit=0, operand_reuse=0)),
+              ("+ masking", gbx.desc_init(masking=1, early_exit=0, operand_reuse=0)),
+              ("+ early exit", gbx.desc_init(masking=1, early_exit=1, operand_reuse=0)),
+              ("+ operand reuse (paper default descriptor)", gbx.desc_init())]
+    tuned, _ = gbx.autotune(g, gbx.TUNE_BFS, synth.sources(n, src, dst, 16, seed=SEED + 100))
+    ladder.append(("+ autotuned thresholds and probe depth", tuned))
+    rows = []
+    for label, d in ladder:
+        r = timed(d)
+        r["step"] = label
+        rows.append(r)
+    for k in range(1, len(rows)):
+        rows[k]["speedup_vs_previous"] = rows[k]["gteps"] / rows[k - 1]["gteps"]
+    # per-level costs in each direction (Figures 5-6) for the first four sources
+    levels = []
+    for s0 in srcs[:4]:
+        per = {}
+        for name, dr in (("push", gbx.DIR_PUSH), ("pull", gbx.DIR_PULL), ("auto", gbx.DIR_AUTO)):
+            d = gbx.Desc.from_buffer_copy(gbx.desc_init(direction=dr, trace=1))
+            gbx.bfs(g, int(s0), depth, parent, d)
+            gbx.bfs(g, int(s0), depth, parent, d)
+            per[name] = gbx.bfs_trace(g)
+        push_t = per["push"]["time_ns"] / 1e3
+        pull_t = per["pull"]["time_ns"] / 1e3
+        best = np.minimum(push_t, pull_t)
+        levels.append({
+            "source": int(s0),
+            "frontier": [int(x) for x in per["push"]["nf"]],
+            "unvisited": [int(x) for x in per["push"]["nu"]],
+            "push_us": [round(float(x), 1) for x in push_t],
+            "pull_us": [round(float(x), 1) for x in pull_t],
+            "pull_examined": [int(x) for x in per["pull"]["e_exam"]],
+            "best_schedule": "".join("P" if a <= b else "L" for a, b in zip(push_t, pull_t)),
+            "auto_schedule": "".join("P" if x == gbx.DIR_PUSH else "L" for x in per["auto"]["direction"]),
+            "best_total_us": round(float(best.sum()), 1),
+            "auto_total_us": round(float(per["auto"]["time_ns"].sum() / 1e3), 1)})
+    out = {"metric": "GTEPS (BASELINE convention) per cumulative optimisation", "unit": UNIT,
+           "graph": {"name": "rmat21-ef48", "vertices": n, "stored_edges": int(nnz), "sources": len(srcs)},
+           "ladder": rows, "tuned_descriptor": gbx.desc_dict(tuned), "per_level": levels,
+           "paper_table2_k40c_gteps": [0.874, 1.411, 1.527, 3.932, 15.83, 42.44]}
+    print(json.dumps(out), flush=True)
+    g.free()
 
 
 def run_reference(args):
@@ -652,7 +738,7 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (0.5 GB CSR, 64 distinct depth+parent pairs per step); no flush",
                    "parallelism": f"replicas x{world}, sources sharded by rank"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic, "kernel": "bfs_kernel<false>",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "bfs_kernel<false, false>",
                      "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs copy bandwidth)",
                      "bytes_per_launch": mean_bytes, "launch_ms": mean_launch_s * 1e3,
                      "frac_of_nominal_7900": achieved / 7900.0},
@@ -681,6 +767,8 @@ def main():
         run_probe(args)
     elif args.sweep:
         run_sweep(args)
+    elif args.ablation:
+        run_ablation(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

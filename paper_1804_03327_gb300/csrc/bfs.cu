@@ -57,12 +57,13 @@ struct BfsArgs {
     int32_t* q[2];
     int32_t* qp[2];
     int32_t* qd[2];
+    int32_t* hfirst;  // per deferred long row: first in-edge index found in the frontier
     LevelCtr* ctr;
     GridBar* bar;
     LevelRec* trace;
     int32_t* status;
     float alpha, beta;
-    int32_t heuristic, mode, early_exit, masking, operand_reuse, symmetric, need_indeg, trace_cap, probe;
+    int32_t heuristic, mode, early_exit, masking, operand_reuse, symmetric, need_indeg, trace_cap, probe, tile_words;
     unsigned long long timeout_ns;
     unsigned int bar_parity;
 };
@@ -141,25 +142,99 @@ __device__ __forceinline__ void push_level(const BfsArgs& a, int32_t L, int cur,
 
 // ---------------------------------------------------------------- pull (Eq 4, Algorithm 2)
 
-constexpr int kPullIlp = 2;  // candidate rows per lane per round (independent probe chains)
+#ifndef GBX_PULL_ILP
+#define GBX_PULL_ILP 2
+#endif
+constexpr int kPullIlp = GBX_PULL_ILP;  // candidate rows per lane per round (independent probe chains)
+// Bitmap words one warp takes at a time in a pull level, a.tile_words: 32, 16 or
+// 8 (lane l holds word l of the tile).  The host picks the width whose round-robin
+// critical path, ceil(tiles / warps) * width, is shortest (ties: the wider), so a
+// graph with fewer 32-word tiles than warps still keeps every warp busy.
+int32_t pull_tile_words(int32_t nwords, long long nwarps) {
+    int32_t best = 32;
+    long long best_cost = -1;
+    for (int32_t tw = 32; tw >= 8; tw >>= 1) {
+        const long long tiles = ((long long)nwords + tw - 1) / tw;
+        const long long cost = (tiles + nwarps - 1) / nwarps * tw;
+        if (best_cost < 0 || cost < best_cost) {
+            best = tw;
+            best_cost = cost;
+        }
+    }
+    return best;
+}
+// A row with more than kPullHugeRow in-edges left after the lane probe is not
+// scanned by the warp that met it: it is listed and, once every tile is done,
+// the whole grid scans its edges in chunks of kPullChunk (a hub row of 10^5+
+// edges would otherwise hold one warp for milliseconds while the rest idle).
+#ifndef GBX_PULL_HUGE_ROW
+#define GBX_PULL_HUGE_ROW 512
+#endif
+#ifndef GBX_PULL_CHUNK
+#define GBX_PULL_CHUNK 1024
+#endif
+constexpr int32_t kPullHugeRow = GBX_PULL_HUGE_ROW;
+constexpr int32_t kPullChunk = GBX_PULL_CHUNK;
 
-// A warp takes a tile of 32 bitmap words (1024 vertices), finds the rows the
-// mask lets through (unvisited, with in-edges), packs them in registers
-// (per-word popcount, warp scan, __fns) and processes them 64 per round, two
-// rows per lane probing in lockstep; rows longer than the probe depth are finished by
-// the whole warp.
+// Deferred long rows of one pull level, kept in the arrays of the queue that the
+// level does not use: row (bitwise NOT of it when the tile phase already found a
+// parent, so the chunks only count examined edges), first edge left, and the
+// ascending prefix of their chunk counts.
+struct HugeRows {
+    int32_t* row;
+    int32_t* k;
+    int32_t* base;
+    int32_t* first;  // smallest edge index with a hit found so far (INT32_MAX: none)
+};
+
+// One warp-wide scan of in_col[kk, kk + 32 * kT) against tbm (kT loads in
+// flight per lane).  Returns the position of the first edge whose source is in
+// tbm (32 * kT if none in range) and that source in *jf.
+template <int kT>
+__device__ __forceinline__ int warp_scan(const int32_t* __restrict__ in_col, const uint32_t* tbm, int32_t kk,
+                                         int32_t ee, int32_t* jf) {
+    const int lane = threadIdx.x & 31;
+    int32_t j[kT];
+#pragma unroll
+    for (int t = 0; t < kT; ++t) {
+        const int32_t idx = kk + 32 * t + lane;
+        j[t] = idx < ee ? __ldg(in_col + idx) : -1;
+    }
+    uint32_t b[kT];
+#pragma unroll
+    for (int t = 0; t < kT; ++t) b[t] = __ballot_sync(0xffffffffu, j[t] >= 0 && bit_test(tbm, j[t]));
+    int pos = 32 * kT;
+    int32_t jsel = j[kT - 1];
+#pragma unroll
+    for (int t = kT - 1; t >= 0; --t) {
+        if (b[t]) {
+            pos = 32 * t + __ffs(b[t]) - 1;
+            jsel = j[t];
+        }
+    }
+    if (pos < 32 * kT) *jf = __shfl_sync(0xffffffffu, jsel, pos & 31);
+    return pos;
+}
+
+// A warp takes a tile of a.tile_words bitmap words, finds the rows the mask
+// lets through (unvisited, with in-edges), packs them in registers (per-word
+// popcount, warp scan, __fns) and processes them 32 * kPullIlp per round, kPullIlp
+// rows per lane probing in lockstep; rows longer than the probe depth are
+// finished by the whole warp, or by the whole grid when they are very long.
+template <bool kHuge>
 __device__ __forceinline__ void pull_level(const BfsArgs& a, int32_t L, int vcur, bool use_fbm, bool append,
-                                           Stage& st, uint32_t* snew, Acc& acc) {
+                                           const HugeRows& hr, Stage& st, uint32_t* snew, Acc& acc) {
     const int lane = threadIdx.x & 31;
     const int gwarp = (int)((blockIdx.x * kBfsThreads + threadIdx.x) >> 5);
     const int nwarps = (int)((gridDim.x * kBfsThreads) >> 5);
     const uint32_t* vprev = a.vis[vcur];
     uint32_t* vnext = a.vis[vcur ^ 1];
     const uint32_t* tbm = use_fbm ? a.fbm : vprev;
-    const int32_t ntiles = (a.nwords + 31) >> 5;
+    const int32_t tw = a.tile_words;
+    const int32_t ntiles = (a.nwords + tw - 1) / tw;
     for (int32_t tile = gwarp; tile < ntiles; tile += nwarps) {
-        const int32_t w = (tile << 5) + lane;
-        const bool wok = w < a.nwords;
+        const int32_t w = tile * tw + lane;
+        const bool wok = lane < tw && w < a.nwords;
         const uint32_t cw = wok ? vprev[w] : 0xffffffffu;
         const uint32_t nz = wok ? a.nz_in[w] : 0u;
         const uint32_t cand = a.masking ? (~cw & nz) : nz;
@@ -191,7 +266,7 @@ __device__ __forceinline__ void pull_level(const BfsArgs& a, int32_t L, int vcur
                 const uint32_t ej = __shfl_sync(0xffffffffu, excl, j);
                 cwj[r] = __shfl_sync(0xffffffffu, cw, j);
                 bitpos[r] = mine[r] ? (int)__fns(cj, 0u, (int)(c - ej) + 1) : 0;
-                i[r] = (((tile << 5) + j) << 5) + bitpos[r];
+                i[r] = ((tile * tw + j) << 5) + bitpos[r];
                 found[r] = false;
                 done[r] = false;
                 par[r] = -1;
@@ -231,7 +306,10 @@ __device__ __forceinline__ void pull_level(const BfsArgs& a, int32_t L, int vcur
 #pragma unroll
                     for (int t = 0; t < 4; ++t) jj[r][t] = t < cnt[r] ? __ldg(a.in_col + k[r] + t) : 0;
                 }
-                if (!(act[0] || act[1])) break;
+                bool any = false;
+#pragma unroll
+                for (int r = 0; r < kPullIlp; ++r) any |= act[r];
+                if (!any) break;
 #pragma unroll
                 for (int r = 0; r < kPullIlp; ++r) {
                     if (!act[r]) continue;
@@ -256,7 +334,8 @@ __device__ __forceinline__ void pull_level(const BfsArgs& a, int32_t L, int vcur
                     k[r] += cnt[r];
                 }
             }
-            // rows longer than the lane probe: the whole warp scans them 32 at a time
+            // rows longer than the lane probe: the whole warp scans them (32, then 128 edges a step),
+            // or lists them for the grid-wide phase when more than kPullHugeRow are left
 #pragma unroll
             for (int r = 0; r < kPullIlp; ++r) {
                 uint32_t pend = __ballot_sync(0xffffffffu, mine[r] && !done[r] && k[r] < end[r]);
@@ -268,23 +347,35 @@ __device__ __forceinline__ void pull_level(const BfsArgs& a, int32_t L, int vcur
                     bool tf = __shfl_sync(0xffffffffu, found[r], t);
                     int32_t tp = __shfl_sync(0xffffffffu, par[r], t);
                     unsigned long long tx = 0;
-                    for (; kk < ee; kk += 32) {
-                        const int32_t idx = kk + lane;
-                        const int32_t j = idx < ee ? __ldg(a.in_col + idx) : 0;
-                        const uint32_t hb = __ballot_sync(0xffffffffu, idx < ee && bit_test(tbm, j));
-                        if (hb) {
-                            const int f = __ffs(hb) - 1;
-                            const int32_t jf = __shfl_sync(0xffffffffu, j, f);
+                    if (kHuge && ee - kk > kPullHugeRow) {
+                        const int32_t row = __shfl_sync(0xffffffffu, i[r], t);
+                        if (lane == 0) {
+                            const unsigned long long nch = (unsigned long long)((ee - kk + kPullChunk - 1) / kPullChunk);
+                            const unsigned long long old = atomicAdd(&st.cout->huge, (nch << 32) | 1ull);
+                            const uint32_t slot = (uint32_t)old;
+                            hr.row[slot] = tf ? ~row : row;
+                            hr.k[slot] = kk;
+                            hr.base[slot] = (int32_t)(old >> 32);
+                            hr.first[slot] = INT32_MAX;
+                        }
+                        kk = ee;
+                    }
+                    // 32 edges first (an early hit then costs no wider read), then 128 at a time
+                    for (int step = 32; kk < ee; kk += step, step = 128) {
+                        int32_t jf = 0;
+                        const int pos = step == 32 ? warp_scan<1>(a.in_col, tbm, kk, ee, &jf)
+                                                   : warp_scan<4>(a.in_col, tbm, kk, ee, &jf);
+                        if (pos < step) {
                             if (!tf) {
                                 tf = true;
                                 tp = jf;
                             }
                             if (a.early_exit) {
-                                tx += (unsigned long long)(f + 1);
+                                tx += (unsigned long long)(pos + 1);
                                 break;
                             }
                         }
-                        tx += (unsigned long long)(ee - kk < 32 ? ee - kk : 32);
+                        tx += (unsigned long long)(ee - kk < step ? ee - kk : step);
                     }
                     if (lane == t) {
                         found[r] = tf;
@@ -322,6 +413,100 @@ __device__ __forceinline__ void pull_level(const BfsArgs& a, int32_t L, int vcur
         __syncwarp();
     }
     if (append) st.flush();
+}
+
+// The grid-wide phase of a pull level: warps take the listed long rows' edge
+// chunks round-robin.  A row is claimed in the next visited bitmap by the first
+// chunk that finds a parent (atomicOr), which writes its depth and parent.  With
+// early exit a chunk records its first hit in hr.first (atomicMin) and chunks
+// that start past a known hit are skipped; with exact_exam (traced runs) only
+// those are, so that pull_huge_exam can count the edges a row-ordered scan
+// examines, otherwise every chunk of a row with a known hit is.
+#ifndef GBX_PULL_HUGE_INLINE
+#define GBX_PULL_HUGE_INLINE __forceinline__
+#endif
+__device__ GBX_PULL_HUGE_INLINE void pull_huge(const BfsArgs& a, int32_t L, int cur, int vcur, int32_t entries,
+                                               int32_t chunks, bool exact_exam, StageBuf* sb, LevelCtr* cout,
+                                               Acc& acc) {
+    const int lane = threadIdx.x & 31;
+    // everything below is rebuilt from the arguments so that little stays live across the level
+    const bool use_fbm = !a.operand_reuse;
+    const bool append = use_fbm;
+    const HugeRows hr{a.q[cur], a.qp[cur], a.qd[cur], a.hfirst};
+    Stage st{sb, 0, cout, a.q[cur ^ 1], a.qp[cur ^ 1], a.qd[cur ^ 1], a.out_ptr, a.in_ptr, 0, a.need_indeg, &acc};
+    const int gwarp = (int)((blockIdx.x * kBfsThreads + threadIdx.x) >> 5);
+    const int nwarps = (int)((gridDim.x * kBfsThreads) >> 5);
+    const uint32_t* vprev = a.vis[vcur];
+    uint32_t* vnext = a.vis[vcur ^ 1];
+    const uint32_t* tbm = use_fbm ? a.fbm : vprev;
+    for (int32_t c = gwarp; c < chunks; c += nwarps) {
+        const int32_t e = warp_find_entry(hr.base, entries, c);
+        const int32_t code = hr.row[e];
+        const bool known = code < 0;
+        const int32_t i = known ? ~code : code;
+        const int32_t rend = __ldg(a.in_ptr + i + 1);
+        const int32_t beg = hr.k[e] + (c - hr.base[e]) * kPullChunk;
+        const int32_t end = rend - beg < kPullChunk ? rend : beg + kPullChunk;
+        if (a.early_exit) {
+            const int32_t fk = ld_volatile_i32(hr.first + e);
+            if (exact_exam ? fk < beg : fk != INT32_MAX) continue;
+        }
+        // rows visited before this level (scanned only without masking) are never new
+        const bool cand = !known && !bit_test(vprev, i);
+        bool hit = false;
+        int32_t par = -1, hit_at = 0;
+        unsigned long long ex = 0;
+        for (int32_t kk = beg; kk < end; kk += 128) {
+            int32_t jf = 0;
+            const int pos = warp_scan<4>(a.in_col, tbm, kk, end, &jf);
+            if (pos < 128) {
+                if (!hit) {
+                    hit = true;
+                    par = jf;
+                    hit_at = kk + pos;
+                }
+                if (a.early_exit) break;
+            }
+            ex += (unsigned long long)(end - kk < 128 ? end - kk : 128);
+        }
+        bool isnew = false;
+        int32_t od = 0;
+        if (lane == 0) {
+            if (a.early_exit) {
+                if (hit) atomicMin(hr.first + e, hit_at);
+            } else {
+                acc.exam += ex;
+            }
+            if (hit && cand) {
+                const uint32_t bit = 1u << (i & 31);
+                isnew = !(atomicOr(vnext + (i >> 5), bit) & bit);
+            }
+            if (isnew) {
+                const int32_t rbeg = __ldg(a.in_ptr + i);
+                a.depth[i] = L + 1;
+                if (a.parent) a.parent[i] = par;
+                od = a.symmetric ? rend - rbeg : __ldg(a.out_ptr + i + 1) - __ldg(a.out_ptr + i);
+                acc.n_new += 1;
+                acc.mf += (unsigned long long)od;
+                acc.indeg += (unsigned long long)(rend - rbeg);
+            }
+        }
+        if (append) st.put(isnew && od > 0, i);
+    }
+    if (append) st.flush();
+}
+
+// Edges a row-ordered scan with early exit examines in the listed rows: up to
+// and including the first hit, or all that were left after the tile phase.
+__device__ __forceinline__ void pull_huge_exam(const BfsArgs& a, const HugeRows& hr, int32_t entries, Acc& acc) {
+    const long long gtid = (long long)blockIdx.x * kBfsThreads + threadIdx.x;
+    for (long long e = gtid; e < entries; e += (long long)gridDim.x * kBfsThreads) {
+        const int32_t code = hr.row[e];
+        const int32_t i = code < 0 ? ~code : code;
+        const int32_t fk = hr.first[e];
+        const int32_t stop = fk != INT32_MAX ? fk + 1 : __ldg(a.in_ptr + i + 1);
+        acc.exam += (unsigned long long)(stop - hr.k[e]);
+    }
 }
 
 // DENSE2SPARSE at a pull -> push switch: F_{L+1} = visited now AND NOT visited before.
@@ -369,7 +554,11 @@ __device__ __forceinline__ void fill_outputs(int32_t* out, int32_t n, int32_t fi
     }
 }
 
-template <bool kTrace>
+// kHuge: long pull rows go to the grid-wide phase.  Launched for runs that
+// expect full row scans (no early exit, or pull on every level); with the
+// direction rule and early exit a pull level rarely meets a long row without a
+// parent, and those runs keep the kernel without that phase (fewer registers).
+template <bool kTrace, bool kHuge>
 __global__ void __launch_bounds__(kBfsThreads, kBfsMinBlocks) bfs_kernel(BfsArgs a) {
     const long long gtid = (long long)blockIdx.x * kBfsThreads + threadIdx.x;
     const long long gstride = (long long)gridDim.x * kBfsThreads;
@@ -404,7 +593,7 @@ __global__ void __launch_bounds__(kBfsThreads, kBfsMinBlocks) bfs_kernel(BfsArgs
 
     __shared__ StageBuf stage_mem[kBfsThreads / 32];
     __shared__ uint32_t tile_new[kBfsThreads / 32][32];
-    __shared__ unsigned long long lvl[5];  // counters of the level just finished, read once per block
+    __shared__ unsigned long long lvl[6];  // counters of the level just finished, read once per block
     const int wib = threadIdx.x >> 5;
     unsigned long long qv = s_od > 0 ? (((unsigned long long)s_od << 32) | 1ull) : 0ull;
     int dir = a.mode == GBX_DIR_PULL ? DIR_PULL : DIR_PUSH;
@@ -437,7 +626,8 @@ __global__ void __launch_bounds__(kBfsThreads, kBfsMinBlocks) bfs_kernel(BfsArgs
                 if (!grid_barrier(barc, gridDim.x, bar_round, a.status, a.timeout_ns)) return;
             }
             appended = use_fbm;
-            pull_level(a, L, vcur, use_fbm, appended, st, tile_new[wib], acc);
+            pull_level<kHuge>(a, L, vcur, use_fbm, appended, HugeRows{a.q[cur], a.qp[cur], a.qd[cur], a.hfirst}, st,
+                       tile_new[wib], acc);
         }
         flush_acc(acc, cout, kTrace);
         if (!grid_barrier(barc, gridDim.x, bar_round, a.status, a.timeout_ns)) return;
@@ -447,8 +637,30 @@ __global__ void __launch_bounds__(kBfsThreads, kBfsMinBlocks) bfs_kernel(BfsArgs
             lvl[2] = ld_volatile_u64(&cout->indeg_new);
             lvl[3] = ld_volatile_u64(&cout->e_exam);
             lvl[4] = ld_volatile_u64(&cout->q);
+            lvl[5] = kHuge ? ld_volatile_u64(&cout->huge) : 0ull;
         }
         __syncthreads();
+        if (kHuge && lvl[5] != 0ull) {  // the pull level listed long rows: the grid scans them now
+            const int32_t entries = (int32_t)(uint32_t)lvl[5];
+            Acc acc2;
+            pull_huge(a, L, cur, vcur, entries, (int32_t)(lvl[5] >> 32), kTrace, stage_mem + wib, cout, acc2);
+            flush_acc(acc2, cout, kTrace);
+            if (!grid_barrier(barc, gridDim.x, bar_round, a.status, a.timeout_ns)) return;
+            if (kTrace && a.early_exit) {
+                Acc acc3;
+                pull_huge_exam(a, HugeRows{a.q[cur], a.qp[cur], a.qd[cur], a.hfirst}, entries, acc3);
+                flush_acc(acc3, cout, true);
+                if (!grid_barrier(barc, gridDim.x, bar_round, a.status, a.timeout_ns)) return;
+            }
+            if (threadIdx.x == 0) {
+                lvl[0] = ld_volatile_u64(&cout->n_new);
+                lvl[1] = ld_volatile_u64(&cout->mf_new);
+                lvl[2] = ld_volatile_u64(&cout->indeg_new);
+                lvl[3] = ld_volatile_u64(&cout->e_exam);
+                lvl[4] = ld_volatile_u64(&cout->q);
+            }
+            __syncthreads();
+        }
         const long long n_new = (long long)lvl[0];
         const long long mf_new = (long long)lvl[1];
         const long long in_new = (long long)lvl[2];
@@ -528,10 +740,14 @@ static gbx_status check_desc(const gbx_desc* d) {
 
 static gbx_status bfs_geometry(Graph* G) {
     if (G->bfs_blocks > 0) return GBX_OK;  // blocks per SM that fit (cached per graph)
-    int b0 = 0, b1 = 0;
-    GBX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, bfs_kernel<false>, kBfsThreads, 0));
-    GBX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, bfs_kernel<true>, kBfsThreads, 0));
-    const int per_sm = b0 < b1 ? b0 : b1;
+    const void* fns[] = {(const void*)bfs_kernel<false, false>, (const void*)bfs_kernel<true, false>,
+                         (const void*)bfs_kernel<false, true>, (const void*)bfs_kernel<true, true>};
+    int per_sm = 1 << 30;
+    for (const void* fn : fns) {
+        int b = 0;
+        GBX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, kBfsThreads, 0));
+        per_sm = b < per_sm ? b : per_sm;
+    }
     GBX_CHECK(per_sm >= 1, GBX_ERR_CUDA, "BFS kernel cannot be resident");
     G->bfs_blocks = per_sm;
     return GBX_OK;
@@ -556,6 +772,7 @@ static gbx_status launch_bfs(Graph* G, int32_t source, int32_t* depth, int32_t* 
     a.vis[0] = G->ws.bm[0];
     a.vis[1] = G->ws.bm[1];
     a.fbm = G->ws.bm[2];
+    a.hfirst = G->ws.list;
     for (int i = 0; i < 2; ++i) {
         a.q[i] = G->ws.q[i];
         a.qp[i] = G->ws.qp[i];
@@ -579,8 +796,11 @@ static gbx_status launch_bfs(Graph* G, int32_t source, int32_t* depth, int32_t* 
     a.timeout_ns = wait_timeout_ns();
     a.bar_parity = G->ws.bar_parity;
     void* args[] = {&a};
-    const void* fn = d.trace ? (const void*)bfs_kernel<true> : (const void*)bfs_kernel<false>;
+    const bool huge = !d.early_exit || d.direction == GBX_DIR_PULL;
+    const void* fn = d.trace ? (huge ? (const void*)bfs_kernel<true, true> : (const void*)bfs_kernel<true, false>)
+                             : (huge ? (const void*)bfs_kernel<false, true> : (const void*)bfs_kernel<false, false>);
     const int per_sm = d.blocks_per_sm > 0 && d.blocks_per_sm < G->bfs_blocks ? d.blocks_per_sm : G->bfs_blocks;
+    a.tile_words = pull_tile_words(G->nwords, (long long)per_sm * G->num_sms * (kBfsThreads / 32));
     GBX_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(per_sm * G->num_sms), dim3(kBfsThreads), args, 0, s));
     G->ws.bar_parity ^= 1u;
     G->ws.last_stream = s;

@@ -55,7 +55,9 @@ struct LevelCtr {
     unsigned long long mf_new;     // out-degree sum of the discovered vertices
     unsigned long long indeg_new;  // in-degree sum of the discovered vertices
     unsigned long long e_exam;     // pull: in-edges examined
-    unsigned long long pad[3];
+    unsigned long long list;       // batched BFS: entries of the level's row list
+    unsigned long long huge;       // pull: deferred long rows (low 32 bits) and their edge chunks (high 32)
+    unsigned long long pad[1];
 };
 
 // Arrival counters of the persistent kernels' grid barrier.  Within one launch a

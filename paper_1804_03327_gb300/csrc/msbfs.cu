@@ -274,7 +274,7 @@ __device__ __forceinline__ void ms_push_scatter(const MsArgs& a, int cur, uint32
                 const uint32_t m = __ballot_sync(0xffffffffu, first);
                 if (m) {
                     unsigned long long base_pos = 0;
-                    if (lane == 0) base_pos = atomicAdd(&cout->pad[0], (unsigned long long)__popc(m));
+                    if (lane == 0) base_pos = atomicAdd(&cout->list, (unsigned long long)__popc(m));
                     base_pos = __shfl_sync(0xffffffffu, base_pos, 0);
                     if (first) a.tlist[base_pos + __popc(m & lanemask_lt())] = v;
                 }
@@ -428,7 +428,7 @@ __global__ void __launch_bounds__(kMsThreads, 1) ms_bfs_kernel(MsArgs a) {
         if (dir == GBX_DIR_PUSH) {
             ms_push_scatter<CW>(a, cur, qcount, qedges, cout);
             if (!grid_barrier(barc, gridDim.x, bar_round, a.status, a.timeout_ns)) return;
-            if (threadIdx.x == 0) lvl[5] = ld_volatile_u64(&cout->pad[0]);
+            if (threadIdx.x == 0) lvl[5] = ld_volatile_u64(&cout->list);
             __syncthreads();
             ms_push_finalize<CW>(a, L, (uint32_t)lvl[5], st, acc);
         } else {
@@ -450,7 +450,7 @@ __global__ void __launch_bounds__(kMsThreads, 1) ms_bfs_kernel(MsArgs a) {
             lvl[1] = ld_volatile_u64(&cout->mf_new);
             lvl[3] = ld_volatile_u64(&cout->e_exam);
             lvl[4] = ld_volatile_u64(&cout->q);
-            lvl[5] = ld_volatile_u64(&cout->pad[0]);
+            lvl[5] = ld_volatile_u64(&cout->list);
         }
         __syncthreads();
         qv = lvl[4];

@@ -46,6 +46,17 @@ def graphs(name):
         elif name == "grid-exact":
             n, s, d = synth.grid_edges(40, 25, p_delete=0.0)
             sym = True
+        elif name in ("hubs", "hubs-directed"):
+            # rows far longer than one warp's share: in-degrees of about 5700 and
+            # 7800 around an RMAT body, so pull levels hand them to the grid-wide phase
+            directed = name == "hubs-directed"
+            n, s, d = synth.rmat_edges(13, 8, seed=11)
+            extra = [(h, np.flatnonzero(synth.vertex_set(n, p, seed=5, stream=h + 1)).astype(np.int32))
+                     for h, p in ((0, 0.7), (1, 0.95))]
+            hs = [s] + [v if directed else np.full(len(v), h, np.int32) for h, v in extra]
+            hd = [d] + [np.full(len(v), h, np.int32) if directed else v for h, v in extra]
+            s, d = np.concatenate(hs), np.concatenate(hd)
+            sym = not directed
         elif name == "er-directed":
             n, s, d = synth.er_edges(300, 0.01, seed=7, directed=True)
             sym = False
@@ -105,6 +116,38 @@ def test_bfs_rmat10_every_toggle(direction, early_exit, masking, operand_reuse):
         depth, parent = run_bfs(g, n, int(src), desc)
         assert np.array_equal(depth, want)
         assert_valid_parents(og.out_ptr, og.out_col, depth, parent, src)
+
+
+@pytest.mark.parametrize("name", ["hubs", "hubs-directed"])
+@pytest.mark.parametrize("direction,early_exit,masking,operand_reuse", TOGGLES)
+def test_bfs_long_rows_every_toggle(name, direction, early_exit, masking, operand_reuse):
+    n, s, d, sym, og, g = graphs(name)
+    desc = gbx.desc_init(direction=direction, early_exit=early_exit, masking=masking, operand_reuse=operand_reuse)
+    for src in list(synth.sources(n, s, d, 3, seed=4)) + [1]:
+        want, _, _ = oracle.bfs(og, src)
+        depth, parent = run_bfs(g, n, int(src), desc)
+        assert np.array_equal(depth, want)
+        assert_valid_parents(og.out_ptr, og.out_col, depth, parent, src)
+
+
+@pytest.mark.parametrize("name", ["hubs", "hubs-directed"])
+def test_trace_long_rows_pull_only(name):
+    # early exit: examined edges equal the row-ordered count even when a long row's
+    # chunks are scanned concurrently; without it every in-edge of every unvisited
+    # row is examined, which is mu (Eq 1)
+    n, s, d, sym, og, g = graphs(name)
+    for src in list(synth.sources(n, s, d, 2, seed=6)) + [1]:
+        want, _, levels = oracle.bfs(og, src)
+        otr = oracle.bfs_trace(og, want, levels)
+        depth, _ = run_bfs(g, n, int(src), gbx.desc_init(direction=gbx.DIR_PULL, trace=1))
+        assert np.array_equal(depth, want)
+        tr = gbx.bfs_trace(g)
+        assert np.array_equal(tr["e_exam"], otr["e_exam"])
+        assert np.array_equal(tr["n_new"], otr["n_new"]) and np.array_equal(tr["mf_new"], otr["mf_new"])
+        depth, _ = run_bfs(g, n, int(src), gbx.desc_init(direction=gbx.DIR_PULL, early_exit=0, trace=1))
+        assert np.array_equal(depth, want)
+        tr = gbx.bfs_trace(g)
+        assert np.array_equal(tr["e_exam"], otr["mu"])
 
 
 @pytest.mark.parametrize("name", ["rmat14", "rmat12-directed", "grid64", "er-directed", "grid-exact"])
