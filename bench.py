@@ -62,8 +62,11 @@ def parse():
     p.add_argument("--ablation", action="store_true",
                    help="Table 2 ladder and per-level push/pull costs on RMAT scale 21 (edge factor 48)")
     p.add_argument("--probe", type=int, default=None, metavar="K",
-                   help="profiling aid: run only source K of the workload --repeat times (for ncu -k bfs_kernel)")
+                   help="profiling aid: run only source K of the workload --repeat times (for ncu -k bfs_kernel); "
+                        "K = -1: source 0 --repeat times, then each workload source once")
     p.add_argument("--repeat", type=int, default=5)
+    p.add_argument("--probe-alpha", type=float, default=None, help="--probe descriptor: alpha (default 0.01)")
+    p.add_argument("--probe-pull-probe", type=int, default=0, help="--probe descriptor: pull_probe")
     return p.parse_args()
 
 
@@ -77,16 +80,28 @@ def run_probe(args):
 
     gbx.load()
     n, src, dst = synth.rmat_edges(args.scale, EDGE_FACTOR, seed=SEED)
-    s = int(rank_sources(n, src, dst, 0)[args.probe])
+    srcs = [int(x) for x in rank_sources(n, src, dst, 0)]
+    s = srcs[max(args.probe, 0)]
     g = gbx.graph_build(n, src, dst)
     depth = torch.empty(n, dtype=torch.int32, device="cuda")
     parent = torch.empty(n, dtype=torch.int32, device="cuda")
+    kw = {"pull_probe": args.probe_pull_probe}
+    if args.probe_alpha is not None:
+        kw["alpha"] = args.probe_alpha
     for _ in range(args.repeat):
-        gbx.bfs(g, s, depth, parent, gbx.desc_init())
+        gbx.bfs(g, s, depth, parent, gbx.desc_init(**kw))
+    listed = srcs if args.probe < 0 else [s]
+    if args.probe < 0:
+        for x in srcs:
+            gbx.bfs(g, x, depth, parent, gbx.desc_init(**kw))
     gbx.graph_sync(g)
-    gbx.bfs(g, s, depth, parent, gbx.desc_init(trace=1))
+    b_alg = []
+    for x in listed:
+        gbx.bfs(g, x, depth, parent, gbx.desc_init(trace=1, **kw))
+        b_alg.append(roofline.bfs_bytes(gbx.bfs_trace(g), n))
     tr = gbx.bfs_trace(g)
-    print(json.dumps({"probe_source": s, "algorithmic_bytes": roofline.bfs_bytes(tr, n),
+    print(json.dumps({"probe_sources": len(listed), "descriptor": kw,
+                      "algorithmic_bytes_mean": float(np.mean(b_alg)),
                       "reached_edges": roofline.reached_edges(tr), **roofline.summary(tr)}))
 
 
