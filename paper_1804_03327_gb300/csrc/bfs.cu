@@ -563,6 +563,8 @@ __global__ void __launch_bounds__(kBfsThreads, kBfsMinBlocks) bfs_kernel(BfsArgs
     const long long gtid = (long long)blockIdx.x * kBfsThreads + threadIdx.x;
     const long long gstride = (long long)gridDim.x * kBfsThreads;
     const int32_t s = a.source;
+    // an error of an earlier launch not yet read by the host: this launch does nothing
+    const int pending = threadIdx.x == 0 ? ld_volatile_i32(a.status + ST_ERROR) : 0;
     unsigned long long t_mark = kTrace && gtid == 0 ? global_timer_ns() : 0ull;
     // Algorithm 1, lines 2-5: f = e_s, v = {s}; outputs initialised
     fill_outputs(a.depth, a.n, -1, s, 0, gtid, gstride);
@@ -589,6 +591,7 @@ __global__ void __launch_bounds__(kBfsThreads, kBfsMinBlocks) bfs_kernel(BfsArgs
     }
     unsigned int* barc = a.bar->count + a.bar_parity;
     unsigned int bar_round = 0;
+    if (__syncthreads_or(pending)) return;
     if (!grid_barrier(barc, gridDim.x, bar_round, a.status, a.timeout_ns)) return;
 
     __shared__ StageBuf stage_mem[kBfsThreads / 32];

@@ -181,6 +181,12 @@ __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
     return v;
 }
 
+__device__ __forceinline__ unsigned int ld_relaxed_u32(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
 __device__ __forceinline__ int ld_volatile_i32(const int32_t* p) { return *(const volatile int32_t*)p; }
 
 __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
@@ -213,40 +219,45 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x)
 }
 
 // Grid-wide barrier for persistent cooperative kernels.  Thread 0 of each block
-// arrives with a release reduction and polls with acquire loads until all
-// nblocks blocks of this round have arrived.  Bounded: a block that waits longer
-// than timeout_ns records GBX_ERR_TIMEOUT in status[ST_ERROR], and every block
-// returns false once any block has recorded an error (a block that sees a
-// pending error does not arrive).  `round` is thread 0's count of barriers
-// passed in this launch.
+// arrives with a release reduction and polls with relaxed loads until all
+// nblocks blocks of this round have arrived, then takes one acquire load of the
+// counter; nothing else is on that path.  Bounded: every 16th poll also reads the
+// status word and the clock; a block that sees an error recorded by another block,
+// or that has waited longer than timeout_ns (it then records GBX_ERR_TIMEOUT in
+// status[ST_ERROR]), returns false, and so does every block still waiting once an
+// error is recorded.  Blocks decide to stop for other reasons (a level cap) all
+// alike, so a completed barrier needs no status check.  `round` is thread 0's
+// count of barriers passed in this launch.
 __device__ __forceinline__ bool grid_barrier(unsigned int* count, unsigned int nblocks, unsigned int& round,
                                              int32_t* status, unsigned long long timeout_ns) {
     __shared__ int ok_shared;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        if (ld_volatile_i32(status + ST_ERROR) != 0) {
-            ok = 0;
-        } else {
-            round += 1;
-            const unsigned int target = round * nblocks;
-            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
-            if ((int)(ld_acquire_u32(count) - target) < 0) {
-                const unsigned long long t0 = global_timer_ns();
-                while ((int)(ld_acquire_u32(count) - target) < 0) {
-                    if (ld_volatile_i32(status + ST_ERROR) != 0) {
-                        ok = 0;
-                        break;
-                    }
-                    if (global_timer_ns() - t0 > timeout_ns) {
-                        atomicCAS(status + ST_ERROR, 0, (int)GBX_ERR_TIMEOUT);
-                        ok = 0;
-                        break;
-                    }
+        round += 1;
+        const unsigned int target = round * nblocks;
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
+        unsigned int spins = 0;
+        unsigned long long t0 = 0ull;
+        // relaxed polls (an acquire on every poll would cost more per iteration), then one
+        // acquire load once the count is reached, which orders everything after the barrier
+        while ((int)(ld_relaxed_u32(count) - target) < 0) {
+            if ((++spins & 15u) == 0u) {
+                if (ld_volatile_i32(status + ST_ERROR) != 0) {
+                    ok = 0;
+                    break;
+                }
+                const unsigned long long now = global_timer_ns();
+                if (t0 == 0ull) {
+                    t0 = now;
+                } else if (now - t0 > timeout_ns) {
+                    atomicCAS(status + ST_ERROR, 0, (int)GBX_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
                 }
             }
-            if (ok && ld_volatile_i32(status + ST_ERROR) != 0) ok = 0;
         }
+        if (ok) (void)ld_acquire_u32(count);
         ok_shared = ok;
     }
     __syncthreads();

@@ -329,6 +329,8 @@ __device__ __forceinline__ void ms_push_finalize(const MsArgs& a, int32_t L, uin
 template <int CW>
 __global__ void __launch_bounds__(kMsThreads, 1) ms_bfs_kernel(MsArgs a) {
     const long long gtid = (long long)blockIdx.x * kMsThreads + threadIdx.x;
+    // an error of an earlier launch not yet read by the host: this launch does nothing
+    const int pending = threadIdx.x == 0 ? ld_volatile_i32(a.status + ST_ERROR) : 0;
     const long long gstride = (long long)gridDim.x * kMsThreads;
     __shared__ StageBuf stage_mem[kMsThreads / 32];
     __shared__ unsigned long long lvl[6];
@@ -370,6 +372,7 @@ __global__ void __launch_bounds__(kMsThreads, 1) ms_bfs_kernel(MsArgs a) {
         a.status[ST_LEVELS] = 0;
         a.bar->count[a.bar_parity ^ 1u] = 0u;
     }
+    if (__syncthreads_or(pending)) return;
     if (!grid_barrier(barc, gridDim.x, bar_round, a.status, a.timeout_ns)) return;
     // ---- sources: lane b starts at src[b] with depth 0
     for (long long b = gtid; b < a.S; b += gstride) {
