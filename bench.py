@@ -267,13 +267,15 @@ def run_sweep(args):
                 vis = torch.from_numpy(synth.vertex_set(n, 1.0 - md, seed=SEED + 1, stream=mi)).cuda()
                 row = {"f": fd, "m_unvisited": md}
                 variants = [("push", gbx.DIR_PUSH, 1, True), ("pull", gbx.DIR_PULL, 0, True),
-                            ("pull_early_exit", gbx.DIR_PULL, 1, True)]
+                            ("pull_early_exit", gbx.DIR_PULL, 1, True),
+                            ("push_sort", gbx.DIR_PUSH, 1, True)]  # Algorithm 3 (gather, sort, reduce, mask)
                 if mi == 0:
                     variants.append(("pull_unmasked", gbx.DIR_PULL, 0, False))  # Eq 2: no mask
                 for label, direction, ee, masked in variants:
                     for fmt in ("dense_u8", "sparse_i32"):
                         uvec = gbx.dense(u8) if fmt == "dense_u8" else gbx.sparse(ulist, ucnt, n)
-                        desc = gbx.desc_init(direction=direction, early_exit=ee, mask_complement=int(masked), trace=1)
+                        desc = gbx.desc_init(direction=direction, early_exit=ee, mask_complement=int(masked), trace=1,
+                                             push_sort=int(label == "push_sort"))
                         mvec = gbx.dense(vis) if masked else None
                         gbx.mxv(gbx.dense(w), mvec, gbx.LOR_LAND, g, uvec, desc)
                         st = gbx.mxv_stats(g)
@@ -301,7 +303,11 @@ def run_sweep(args):
             xs = [r["f"] for r in pts if r["pull_early_exit_dense_u8_ms"] < r["push_dense_u8_ms"]]
             cross[f"{md:.3g}"] = min(xs) if xs else None
         best = max(max(r[k] for k in r if k.endswith("_gbs")) for r in res)
+        # Algorithm 3's sort-based push against the one-pass bitmap claim, per frontier density
+        sort_ratio = {f"{fd:.3g}": float(np.median([r["push_sort_sparse_i32_ms"] / r["push_sparse_i32_ms"]
+                                                    for r in res if r["f"] == fd])) for fd in fdens}
         out["graphs"][name] = {"points": res, "pull_beats_push_from_frontier_density": cross,
+                               "push_sort_time_over_push_time": sort_ratio,
                                "best_gbs": best, "best_frac": best / peak}
         g.free()
     print(json.dumps(out), flush=True)

@@ -157,12 +157,17 @@ typedef struct {
     int32_t pull_probe;      /* BFS pull: in-neighbours one lane scans before its warp takes the row over
                                 (0 = default: 16 single-source, 8 batched; otherwise 4..1024) */
     int32_t blocks_per_sm;   /* BFS kernels: persistent blocks per SM (0 = as many as fit) */
-    int32_t reserved[3];     /* must be 0 */
+    int32_t push_sort;       /* gbx_mxv push: 1 = Algorithm 3 / Section 6.2 (gather the selected columns,
+                                key-only radix sort, segmented reduction, mask) instead of the one-pass
+                                bitmap claim; same result.  Takes the AUTO decision on the host (one
+                                stream synchronisation) and allocates its sort buffers per call.
+                                gbx_bfs and gbx_bfs_batch reject 1 (GBX_ERR_NOT_SUPPORTED). */
+    int32_t reserved[2];     /* must be 0 */
 } gbx_desc;
 
 /* Defaults: transpose 1, mask_complement 0, early_exit 1, accum 0,
  * direction AUTO, heuristic RATIO, alpha = beta = 0.01 (Section 6.3),
- * masking 1, operand_reuse 1, trace 0, pull_probe 0, blocks_per_sm 0. */
+ * masking 1, operand_reuse 1, trace 0, pull_probe 0, blocks_per_sm 0, push_sort 0. */
 void gbx_desc_init(gbx_desc* d);
 
 /* ------------------------------------------------------------------ matvec */

@@ -737,7 +737,8 @@ static gbx_status check_desc(const gbx_desc* d) {
     GBX_CHECK(d->pull_probe == 0 || (d->pull_probe >= 4 && d->pull_probe <= 1024), GBX_ERR_INVALID_VALUE,
               "desc.pull_probe must be 0 or in [4, 1024]");
     GBX_CHECK(d->blocks_per_sm >= 0, GBX_ERR_INVALID_VALUE, "desc.blocks_per_sm must be >= 0");
-    for (int k = 0; k < 3; ++k) GBX_CHECK(d->reserved[k] == 0, GBX_ERR_INVALID_VALUE, "desc.reserved must be 0");
+    GBX_CHECK(d->push_sort == 0, GBX_ERR_NOT_SUPPORTED, "desc.push_sort applies to gbx_mxv only");
+    for (int k = 0; k < 2; ++k) GBX_CHECK(d->reserved[k] == 0, GBX_ERR_INVALID_VALUE, "desc.reserved must be 0");
     return GBX_OK;
 }
 

@@ -155,6 +155,18 @@ gbx_status exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t count_max
 
 // Stable LSD radix sort of 64-bit keys on the low `bits` bits; result in *keys (buffers swapped as needed).
 gbx_status radix_sort_u64(unsigned long long** keys, unsigned long long** alt, int64_t n, int bits, cudaStream_t s);
+// The same for 32-bit keys (the key-only sort of Algorithm 3's multiway merge).
+gbx_status radix_sort_u32(uint32_t** keys, uint32_t** alt, int64_t n, int bits, cudaStream_t s);
+
+struct Graph;
+// Column-based matvec as Algorithm 3 (mxv_sort.cu): the columns of u's `count`
+// entries (ulist, entries at or past `cap` expand nothing) are gathered, sorted,
+// reduced and masked by pass_bm (NULL: all pass).  Output either as a sorted list
+// (out_list + device count out_count) or as bits set in R (out_list NULL).
+// *edges receives the number of gathered entries.  Synchronises `s` once.
+gbx_status mxv_push_sorted(Graph* G, const int32_t* push_ptr, const int32_t* push_col, const int32_t* ulist,
+                           int32_t count, int32_t cap, const uint32_t* pass_bm, uint32_t* R, int32_t* out_list,
+                           int32_t* out_count, int64_t* edges, cudaStream_t s);
 
 // Bitmap helpers.
 gbx_status pack_dense_to_bitmap(const uint8_t* dense, int32_t n, uint32_t invert, uint32_t* bm, cudaStream_t s);

@@ -612,6 +612,7 @@ extern "C" gbx_status gbx_bfs_batch(gbx_graph* g, const int32_t* sources, int32_
     GBX_CHECK(d.alpha >= 0.0f && d.alpha == d.alpha, GBX_ERR_INVALID_VALUE, "desc.alpha must be >= 0");
     GBX_CHECK(d.pull_probe == 0 || (d.pull_probe >= 4 && d.pull_probe <= 1024), GBX_ERR_INVALID_VALUE,
               "desc.pull_probe must be 0 or in [4, 1024]");
+    GBX_CHECK(d.push_sort == 0, GBX_ERR_NOT_SUPPORTED, "desc.push_sort applies to gbx_mxv only");
     cudaStream_t s = (cudaStream_t)stream;
     GBX_TRY(ms_reserve(G->ws, G->n, S, s));
     if (G->ws.ms_src_cap < S) {

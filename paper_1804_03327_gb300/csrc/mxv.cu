@@ -333,6 +333,11 @@ __global__ void zero_stats_kernel(MxvStats* s) {
     *s = z;
 }
 
+__global__ void set_push_stats_kernel(MxvStats* s, int32_t ucount, int64_t edges) {
+    s->ucount = (unsigned long long)ucount;
+    s->edges = (unsigned long long)edges;
+}
+
 static gbx_status check_vec(const gbx_vector* v, int32_t n, const char* name, bool output) {
     GBX_CHECK(v->format == GBX_DENSE || v->format == GBX_SPARSE, GBX_ERR_INVALID_VALUE,
               std::string(name) + ": unknown format");
@@ -372,7 +377,8 @@ extern "C" gbx_status gbx_mxv(gbx_vector* w, const gbx_vector* mask, int32_t sem
         gbx_desc_init(&d);
     GBX_CHECK(d.direction >= GBX_DIR_AUTO && d.direction <= GBX_DIR_PULL, GBX_ERR_INVALID_VALUE, "desc.direction");
     GBX_CHECK(d.alpha >= 0.0f && d.alpha == d.alpha, GBX_ERR_INVALID_VALUE, "desc.alpha must be >= 0");
-    for (int k = 0; k < 3; ++k) GBX_CHECK(d.reserved[k] == 0, GBX_ERR_INVALID_VALUE, "desc.reserved must be 0");
+    GBX_CHECK(d.push_sort == 0 || d.push_sort == 1, GBX_ERR_INVALID_VALUE, "desc.push_sort must be 0 or 1");
+    for (int k = 0; k < 2; ++k) GBX_CHECK(d.reserved[k] == 0, GBX_ERR_INVALID_VALUE, "desc.reserved must be 0");
     cudaStream_t s = (cudaStream_t)stream;
 
     // w = A' u with A' = A^T (transpose) or A.  Pull reads rows of A' (CSR of A'),
@@ -392,9 +398,9 @@ extern "C" gbx_status gbx_mxv(gbx_vector* w, const gbx_vector* mask, int32_t sem
     MxvStats* stats = d.trace ? reinterpret_cast<MxvStats*>(G->ws.ctr + 3) : nullptr;
     if (stats) zero_stats_kernel<<<1, 1, 0, s>>>(stats);
 
-    const int dir = d.direction;
-    const bool want_pull = dir != GBX_DIR_PUSH;
-    const bool want_push = dir != GBX_DIR_PULL;
+    int dir = d.direction;
+    bool want_pull = dir != GBX_DIR_PUSH;
+    bool want_push = dir != GBX_DIR_PULL;
 
     // u as a bitmap (pull) and as a sorted list (push)
     const int32_t* ulist = nullptr;
@@ -430,9 +436,35 @@ extern "C" gbx_status gbx_mxv(gbx_vector* w, const gbx_vector* mask, int32_t sem
         if (d.mask_complement) GBX_TRY(invert_bitmap(pass, n, s));
         pass_bm = pass;
     }
+    // Algorithm 3 (desc.push_sort): sizes its scratch from the frontier, so the
+    // frontier size and the AUTO decision are taken on the host
+    bool sorted_done = false;
+    if (d.push_sort && want_push && !nothing_passes) {
+        int32_t hc = 0;
+        GBX_CUDA_TRY(cudaMemcpyAsync(&hc, ucount, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        GBX_CUDA_TRY(cudaStreamSynchronize(s));
+        if (dir == GBX_DIR_PUSH || (double)hc / (double)n <= (double)d.alpha) {
+            const int32_t count = hc < 0 ? 0 : (hc > n ? n : hc);
+            const bool direct = w->format == GBX_SPARSE && !d.accum;  // the sorted list is w itself
+            if (!direct) GBX_TRY(fill_bitmap(R, n, 0u, s));
+            int64_t edges = 0;
+            GBX_TRY(mxv_push_sorted(G, push_ptr, push_col, ulist, count, ucap, pass_bm, direct ? nullptr : R,
+                                    direct ? (int32_t*)w->data : nullptr, direct ? w->nnz : nullptr, &edges, s));
+            if (stats) set_push_stats_kernel<<<1, 1, 0, s>>>(stats, count, edges);
+            if (direct) {
+                GBX_CUDA_TRY(cudaGetLastError());
+                G->ws.last_stream = s;
+                return GBX_OK;
+            }
+            sorted_done = true;
+        } else {
+            dir = GBX_DIR_PULL;
+            want_push = false;
+        }
+    }
     // a pull writes every result word; push accumulates into a cleared bitmap
-    if (want_push || nothing_passes) GBX_TRY(fill_bitmap(R, n, 0u, s));
-    if (!nothing_passes) {
+    if (!sorted_done && (want_push || nothing_passes)) GBX_TRY(fill_bitmap(R, n, 0u, s));
+    if (!nothing_passes && !sorted_done) {
         const int32_t* flag = nullptr;
         if (dir == GBX_DIR_AUTO) {
             mxv_decide_kernel<<<1, 1, 0, s>>>(ucount, n, d.alpha, dflag);

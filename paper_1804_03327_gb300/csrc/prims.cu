@@ -1,5 +1,5 @@
 // Device primitives used by the graph build and the matvec operators:
-// a three-phase exclusive scan, a stable LSD radix sort of 64-bit keys, and
+// a three-phase exclusive scan, a stable LSD radix sort of 64- or 32-bit keys, and
 // bitmap <-> dense / sorted-list conversions (the DENSE2SPARSE / SPARSE2DENSE
 // vector conversions of Section 6.3, on bit-packed vectors).
 #include "gbx_internal.cuh"
@@ -112,8 +112,9 @@ constexpr int kSortThreads = 256;
 constexpr int kSortRounds = 16;
 constexpr int kSortTile = kSortThreads * kSortRounds;  // keys per block
 
-__global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const unsigned long long* __restrict__ keys, int64_t n,
-                                                                   int shift, int32_t* __restrict__ hist, int nblocks) {
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const K* __restrict__ keys, int64_t n, int shift,
+                                                                   int32_t* __restrict__ hist, int nblocks) {
     __shared__ uint32_t cnt[256];
     cnt[threadIdx.x] = 0;
     __syncthreads();
@@ -127,10 +128,10 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const unsigned
 }
 
 // Stable scatter: keys are ranked by (round, warp, lane), i.e. by input order.
-__global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(const unsigned long long* __restrict__ in,
-                                                                      unsigned long long* __restrict__ out, int64_t n,
-                                                                      int shift, const int32_t* __restrict__ offs_all,
-                                                                      int nblocks) {
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(const K* __restrict__ in, K* __restrict__ out,
+                                                                      int64_t n, int shift,
+                                                                      const int32_t* __restrict__ offs_all, int nblocks) {
     constexpr int kWarps = kSortThreads / 32;
     __shared__ uint32_t offs[256];
     __shared__ uint32_t wcnt[kWarps][256];
@@ -143,7 +144,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(const unsig
         __syncthreads();
         const int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
         const bool valid = i < n;
-        unsigned long long key = 0;
+        K key = 0;
         uint32_t d = 0, rank = 0;
         const uint32_t act = __ballot_sync(0xffffffffu, valid);
         if (valid) {
@@ -168,7 +169,8 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(const unsig
     }
 }
 
-gbx_status radix_sort_u64(unsigned long long** keys, unsigned long long** alt, int64_t n, int bits, cudaStream_t s) {
+template <typename K>
+static gbx_status radix_sort(K** keys, K** alt, int64_t n, int bits, cudaStream_t s) {
     if (n <= 1) return GBX_OK;
     const int nblocks = (int)((n + kSortTile - 1) / kSortTile);
     const int64_t hn = (int64_t)nblocks * 256;
@@ -182,11 +184,11 @@ gbx_status radix_sort_u64(unsigned long long** keys, unsigned long long** alt, i
     }
     gbx_status st = GBX_OK;
     for (int shift = 0; shift < bits && st == GBX_OK; shift += 8) {
-        radix_hist_kernel<<<nblocks, kSortThreads, 0, s>>>(*keys, n, shift, hist, nblocks);
+        radix_hist_kernel<K><<<nblocks, kSortThreads, 0, s>>>(*keys, n, shift, hist, nblocks);
         st = exclusive_scan_i32(hist, hist, hn, nullptr, tmp, s);
         if (st != GBX_OK) break;
-        radix_scatter_kernel<<<nblocks, kSortThreads, 0, s>>>(*keys, *alt, n, shift, hist, nblocks);
-        unsigned long long* t = *keys;
+        radix_scatter_kernel<K><<<nblocks, kSortThreads, 0, s>>>(*keys, *alt, n, shift, hist, nblocks);
+        K* t = *keys;
         *keys = *alt;
         *alt = t;
     }
@@ -196,6 +198,14 @@ gbx_status radix_sort_u64(unsigned long long** keys, unsigned long long** alt, i
     if (st != GBX_OK) return st;
     GBX_CUDA_TRY(le);
     return GBX_OK;
+}
+
+gbx_status radix_sort_u64(unsigned long long** keys, unsigned long long** alt, int64_t n, int bits, cudaStream_t s) {
+    return radix_sort<unsigned long long>(keys, alt, n, bits, s);
+}
+
+gbx_status radix_sort_u32(uint32_t** keys, uint32_t** alt, int64_t n, int bits, cudaStream_t s) {
+    return radix_sort<uint32_t>(keys, alt, n, bits, s);
 }
 
 // ---------------------------------------------------------------- bitmaps

@@ -74,7 +74,7 @@ class Desc(ctypes.Structure):
                 ("accum", ctypes.c_int32), ("direction", ctypes.c_int32), ("heuristic", ctypes.c_int32),
                 ("alpha", ctypes.c_float), ("beta", ctypes.c_float), ("masking", ctypes.c_int32),
                 ("operand_reuse", ctypes.c_int32), ("trace", ctypes.c_int32), ("pull_probe", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("blocks_per_sm", ctypes.c_int32), ("push_sort", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class Level(ctypes.Structure):

@@ -53,7 +53,7 @@ def test_desc_defaults_follow_section_6_3(lib):
     assert d.mask_complement == 0 and d.accum == 0 and d.trace == 0
     assert d.direction == gbx.DIR_AUTO and d.heuristic == gbx.HEUR_RATIO
     assert abs(d.alpha - 0.01) < 1e-7 and abs(d.beta - 0.01) < 1e-7
-    assert d.pull_probe == 0 and d.blocks_per_sm == 0 and list(d.reserved) == [0] * 3
+    assert d.pull_probe == 0 and d.blocks_per_sm == 0 and d.push_sort == 0 and list(d.reserved) == [0] * 2
 
 
 def test_status_names_and_version(lib):

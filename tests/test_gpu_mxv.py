@@ -166,3 +166,78 @@ def test_mxv_rejects_bad_arguments():
     with pytest.raises(gbx.GbxError) as e:  # sparse output needs capacity >= n
         gbx.mxv(gbx.sparse(idx, c, n), None, gbx.LOR_LAND, g, gbx.dense(t))
     assert e.value.status == gbx.ERR_INVALID_VALUE
+
+
+# ---- Algorithm 3: the paper's sort-based push (desc.push_sort) gives the same w
+
+SORT_CASES = list(itertools.product(
+    [gbx.DIR_PUSH, gbx.DIR_AUTO],  # direction (AUTO with alpha 1 always pushes)
+    [0, 1],                        # transpose
+    ["none", "dense", "sparse"],   # mask
+    [0, 1],                        # complement
+    [0, 1],                        # accum
+))
+
+
+@pytest.mark.parametrize("direction,transpose,mask_kind,complement,accum", SORT_CASES)
+def test_mxv_sorted_push_all_flags(direction, transpose, mask_kind, complement, accum):
+    for name in ["rmat11", "rmat11-directed"]:
+        n, og, g = graph(name)
+        for k, (ud, md) in enumerate([(0.001, 0.5), (0.02, 0.9), (0.3, 0.1)]):
+            u = synth.vertex_set(n, ud, seed=40 + k)
+            m = synth.vertex_set(n, md, seed=50 + k)
+            w_old = synth.vertex_set(n, 0.2, seed=60 + k)
+            want = oracle.mxv(n, n, og.out_ptr, og.out_col, u, None if mask_kind == "none" else m,
+                              transpose=bool(transpose), complement=bool(complement), accum=bool(accum),
+                              w_old=w_old)
+            for ufmt, wfmt in [(gbx.DENSE, gbx.DENSE), (gbx.SPARSE, gbx.SPARSE), (gbx.DENSE, gbx.SPARSE)]:
+                uv, ukeep = to_vec(u, ufmt, n)
+                mv = None
+                if mask_kind != "none":
+                    mv, mkeep = to_vec(m, gbx.DENSE if mask_kind == "dense" else gbx.SPARSE, n)
+                wv, wkeep = out_vec(wfmt, n, w_old)
+                desc = gbx.desc_init(direction=direction, transpose=transpose, mask_complement=complement,
+                                     accum=accum, push_sort=1, alpha=1.0)
+                gbx.mxv(wv, mv, gbx.LOR_LAND, g, uv, desc)
+                assert np.array_equal(read_vec(wv, wkeep, wfmt, n), want), (name, k, ufmt, wfmt)
+
+
+def test_mxv_sorted_push_large_and_extremes():
+    """Many gather tiles and radix passes (RMAT scale 16 with hubs; the 50x41 grid,
+    n not a multiple of 32), empty and full frontiers, empty and full masks."""
+    n16, s16, d16 = synth.rmat_edges(16, 16, seed=8)
+    og16 = oracle.graph(n16, s16, d16)
+    g16 = gbx.graph_build(n16, s16, d16)
+    n, og, g = graph("grid")
+    for (nn, ogx, gx) in [(n16, og16, g16), (n, og, g)]:
+        for ud in [0.0, 1e-3, 0.5, 1.0]:
+            u = synth.vertex_set(nn, ud, seed=13) if 0 < ud < 1 else np.full(nn, int(ud), np.uint8)
+            for md in [0.0, 0.5, 1.0]:
+                m = synth.vertex_set(nn, md, seed=14) if 0 < md < 1 else np.full(nn, int(md), np.uint8)
+                want = oracle.mxv(nn, nn, ogx.out_ptr, ogx.out_col, u, m, transpose=True, complement=True)
+                uv, uk = to_vec(u, gbx.SPARSE, nn)
+                mv, mk = to_vec(m, gbx.DENSE, nn)
+                wv, wk = to_vec(np.zeros(nn, np.uint8), gbx.SPARSE, nn)
+                gbx.mxv(wv, mv, gbx.LOR_LAND, gx, uv,
+                        gbx.desc_init(direction=gbx.DIR_PUSH, mask_complement=1, push_sort=1, trace=1))
+                assert np.array_equal(read_vec(wv, wk, gbx.SPARSE, nn), want), (nn, ud, md)
+                st = gbx.mxv_stats(gx)
+                deg = np.diff(ogx.out_ptr)
+                assert st["u_nnz"] == u.sum() and st["edges"] == deg[u.astype(bool)].sum()
+    g16.free()
+
+
+def test_push_sort_is_mxv_only():
+    n, og, g = graph("rmat11")
+    depth = torch.zeros(n, dtype=torch.int32, device="cuda")
+    with pytest.raises(gbx.GbxError) as e:
+        gbx.bfs(g, 0, depth, None, gbx.desc_init(push_sort=1))
+    assert e.value.status == gbx.ERR_NOT_SUPPORTED
+    with pytest.raises(gbx.GbxError) as e:
+        gbx.bfs_batch(g, np.array([0, 1], np.int32), torch.zeros((2, n), dtype=torch.int32, device="cuda"),
+                      desc=gbx.desc_init(push_sort=1))
+    assert e.value.status == gbx.ERR_NOT_SUPPORTED
+    t = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    with pytest.raises(gbx.GbxError) as e:
+        gbx.mxv(gbx.dense(t), None, gbx.LOR_LAND, g, gbx.dense(torch.zeros_like(t)), gbx.desc_init(push_sort=2))
+    assert e.value.status == gbx.ERR_INVALID_VALUE
