@@ -16,10 +16,17 @@ written in Python:
 * ``ms_bfs``: many sources as independent single-source BFS runs (one lane
   per source), the definition the bit-parallel batched form must reproduce.
 
+The (min, +) semiring of Section 5.6 (weighted graphs, ``mxv_minplus`` in
+double, ``sssp`` as Bellman-Ford with binary32 sums) is in ``oracle.c`` too.
+
 Pins (tests/test_oracle_pins.py): brute-force dense Boolean matvec BFS on
 n <= 64, closed forms (grid Manhattan distance, path, star, complete graph),
 BFS invariants, scipy's BFS as an outside library, dense-matrix mxv for every
-flag combination, and the Figure 3 worked example (tests/golden/).
+flag combination, and the Figure 3 worked example (tests/golden/).  The
+(min, +) functions: weights against a Python dictionary of pairs; the matvec
+against the Boolean oracle (zero weights), unit vectors (a column of weights)
+and tropical linearity; SSSP against scipy's Dijkstra (exact on integer
+weights), the BFS depth (unit weights) and the Bellman optimality conditions.
 Parity unpinned: none of the functions below.
 """
 from __future__ import annotations
@@ -66,6 +73,10 @@ def _load():
             lib.oracle_bfs_trace.argtypes = [i32, p, p, p, p, i32, p, i32]
             lib.oracle_mxv.restype = ctypes.c_int
             lib.oracle_mxv.argtypes = [i32, i32, p, p, i32, p, p, i32, i32, p]
+            lib.oracle_csr_weights.argtypes = [i32, i64, p, p, p, i32, i32, p, p, p]
+            lib.oracle_transpose_weighted.argtypes = [i32, p, p, p, p, p, p]
+            lib.oracle_mxv_minplus.argtypes = [i32, i32, p, p, p, i32, p, p, i32, i32, p]
+            lib.oracle_sssp_bf.argtypes = [i32, p, p, p, i32, p]
             _lib = lib
     return _lib
 
@@ -217,3 +228,62 @@ def ms_bfs(g: Graph, sources) -> np.ndarray:
     for k, s in enumerate(sources):
         out[k], _, _ = bfs(g, s)
     return out
+
+
+class WeightedGraph(Graph):
+    """Graph with edge weights: out_val[k] belongs to out_col[k], in_val[k] to in_col[k]
+    (double; every value is a binary32 input weight)."""
+
+    def __init__(self, n, out_ptr, out_col, out_val, in_ptr, in_col, in_val):
+        super().__init__(n, out_ptr, out_col, in_ptr, in_col)
+        self.out_val, self.in_val = out_val, in_val
+
+
+def graph_weighted(n: int, src, dst, w, symmetrize: bool = True, drop_self_loops: bool = True) -> WeightedGraph:
+    """Weighted CSR of A and of A^T; parallel pairs keep the smallest weight."""
+    src, dst = _i32(src), _i32(dst)
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    out_ptr, out_col = csr_build(n, src, dst, symmetrize, drop_self_loops)
+    out_val = np.empty(max(1, len(out_col)), dtype=np.float64)
+    if _load().oracle_csr_weights(n, len(src), _p(src), _p(dst), _p(w), int(symmetrize), int(drop_self_loops),
+                                  _p(out_ptr), _p(out_col), _p(out_val)) != 0:
+        raise ValueError("oracle_csr_weights: the CSR does not match the edge list")
+    out_val = out_val[:len(out_col)].copy()
+    if symmetrize:
+        return WeightedGraph(n, out_ptr, out_col, out_val, out_ptr, out_col, out_val)
+    in_ptr = np.empty(n + 1, dtype=np.int32)
+    in_col = np.empty(max(1, len(out_col)), dtype=np.int32)
+    in_val = np.empty(max(1, len(out_col)), dtype=np.float64)
+    if _load().oracle_transpose_weighted(n, _p(out_ptr), _p(out_col), _p(out_val), _p(in_ptr), _p(in_col),
+                                         _p(in_val)) != 0:
+        raise MemoryError("oracle_transpose_weighted failed")
+    return WeightedGraph(n, out_ptr, out_col, out_val, in_ptr, in_col[:len(out_col)].copy(),
+                         in_val[:len(out_col)].copy())
+
+
+def mxv_minplus(nrows: int, ncols: int, row_ptr, col, val, u, mask=None, transpose: bool = False,
+                complement: bool = False, accum: bool = False, w_old=None) -> np.ndarray:
+    """float64 result of the masked (min, +) matvec; +inf marks an absent entry."""
+    nin = nrows if transpose else ncols
+    nout = ncols if transpose else nrows
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    assert u.shape == (nin,)
+    m = None if mask is None else to_dense(mask, nout)
+    w = np.full(nout, np.inf) if w_old is None else np.ascontiguousarray(w_old, dtype=np.float64).copy()
+    rc = _load().oracle_mxv_minplus(nrows, ncols, _p(_i32(row_ptr)), _p(_i32(col)),
+                                    _p(np.ascontiguousarray(val, dtype=np.float64)), int(transpose), _p(u), _p(m),
+                                    int(complement), int(accum), _p(w))
+    if rc != 0:
+        raise MemoryError("oracle_mxv_minplus failed")
+    return w
+
+
+def sssp(g: WeightedGraph, source: int):
+    """Bellman-Ford distances (float32, +inf unreached) over out-edges, and the
+    number of iterations that changed them."""
+    d = np.empty(g.n, dtype=np.float32)
+    val32 = np.ascontiguousarray(g.out_val, dtype=np.float32)
+    it = _load().oracle_sssp_bf(g.n, _p(g.out_ptr), _p(g.out_col), _p(val32), int(source), _p(d))
+    if it < 0:
+        raise MemoryError("oracle_sssp_bf failed")
+    return d, int(it)

@@ -19,6 +19,13 @@
  *   - oracle_mxv: masked matvec by its definition, Eq 2-5 over the Boolean
  *     semiring ({0,1}, OR, AND, 0) of Algorithm 1, with the structural
  *     complement (Section 3.2) and accumulate flag of Algorithm 2.
+ *   - oracle_csr_weights / oracle_mxv_minplus / oracle_sssp_bf: the generalised
+ *     semiring of Section 4 (D, x, +, I) instantiated as (R u {+inf}, +, min,
+ *     +inf), the tropical semiring Section 5.6 names for SSSP: edge weights on
+ *     the CSR (duplicates keep the smallest weight), the masked matvec over it
+ *     in double precision, and Bellman-Ford as the repeated matvec
+ *     d <- min(d, A^T d) until nothing changes, with every addition rounded to
+ *     binary32 (the precision the device computes in).
  * Pins: tests/test_oracle_pins.py checks each function against brute force,
  * closed forms and invariants that do not come from this file.
  */
@@ -212,4 +219,134 @@ int oracle_mxv(int32_t nrows, int32_t ncols, const int32_t* row_ptr, const int32
     }
     free(t);
     return 0;
+}
+
+/*
+ * Weights of the CSR (row_ptr, col) built by oracle_csr_build from the same edge
+ * list: val[k] = the smallest w[e] over input pairs e that map to entry k (the
+ * pair itself, and its reverse when symmetrising).  Entries are located by a
+ * linear scan of the row (rows are sorted; this is the slow, plain way).
+ * Returns 0, or -1 if a pair has no entry (the CSR was not built from this list).
+ */
+int oracle_csr_weights(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, const float* w,
+                       int32_t symmetrize, int32_t drop_self_loops, const int32_t* row_ptr, const int32_t* col,
+                       double* val) {
+    const int64_t nnz = row_ptr[n];
+    for (int64_t k = 0; k < nnz; ++k) val[k] = 1.0 / 0.0;
+    for (int64_t e = 0; e < m; ++e) {
+        if (drop_self_loops && src[e] == dst[e]) continue;
+        for (int dir = 0; dir < (symmetrize ? 2 : 1); ++dir) {
+            const int32_t r = dir ? dst[e] : src[e];
+            const int32_t c = dir ? src[e] : dst[e];
+            int64_t at = -1;
+            for (int64_t k = row_ptr[r]; k < row_ptr[r + 1]; ++k)
+                if (col[k] == c) {
+                    at = k;
+                    break;
+                }
+            if (at < 0) return -1;
+            if ((double)w[e] < val[at]) val[at] = (double)w[e];
+        }
+    }
+    return 0;
+}
+
+/* Transpose of a weighted CSR: entry (r, c, v) becomes (c, r, v), rows ascending. */
+int oracle_transpose_weighted(int32_t n, const int32_t* row_ptr, const int32_t* col, const double* val,
+                              int32_t* t_row_ptr, int32_t* t_col, double* t_val) {
+    const int64_t nnz = row_ptr[n];
+    for (int32_t i = 0; i <= n; ++i) t_row_ptr[i] = 0;
+    for (int64_t k = 0; k < nnz; ++k) t_row_ptr[col[k] + 1] += 1;
+    for (int32_t i = 0; i < n; ++i) t_row_ptr[i + 1] += t_row_ptr[i];
+    int32_t* cur = (int32_t*)malloc(((size_t)n + 1) * sizeof(int32_t));
+    if (!cur) return -2;
+    memcpy(cur, t_row_ptr, ((size_t)n + 1) * sizeof(int32_t));
+    /* rows r visited in ascending order, so each transposed row comes out sorted */
+    for (int32_t r = 0; r < n; ++r)
+        for (int64_t k = row_ptr[r]; k < row_ptr[r + 1]; ++k) {
+            const int32_t p = cur[col[k]]++;
+            t_col[p] = r;
+            t_val[p] = val[k];
+        }
+    free(cur);
+    return 0;
+}
+
+/*
+ * Masked matvec over (R u {+inf}, +, min, +inf), in double:
+ *   t(i) = min over j with A'(i, j) of ( A'(i, j) + u(j) ),  +inf if there is none,
+ *   A' = A^T when `transpose` (then t(c) takes the entries (r, c) of A), else A;
+ *   pass(i) = (mask(i) != 0, or 1 without a mask) XOR complement;
+ *   w(i) = pass(i) ? (accum ? min(w_old(i), t(i)) : t(i)) : (accum ? w_old(i) : +inf).
+ * An absent entry of u, w or the result is +inf (the semiring's identity).
+ */
+int oracle_mxv_minplus(int32_t nrows, int32_t ncols, const int32_t* row_ptr, const int32_t* col, const double* val,
+                       int32_t transpose, const double* u, const uint8_t* mask, int32_t complement, int32_t accum,
+                       double* w) {
+    const int32_t nout = transpose ? ncols : nrows;
+    const double inf = 1.0 / 0.0;
+    double* t = (double*)malloc((size_t)(nout > 0 ? nout : 1) * sizeof(double));
+    if (!t) return -2;
+    for (int32_t i = 0; i < nout; ++i) t[i] = inf;
+    for (int32_t r = 0; r < nrows; ++r) {
+        for (int64_t k = row_ptr[r]; k < row_ptr[r + 1]; ++k) {
+            const int32_t c = col[k];
+            if (transpose) {
+                const double x = val[k] + u[r];
+                if (x < t[c]) t[c] = x;
+            } else {
+                const double x = val[k] + u[c];
+                if (x < t[r]) t[r] = x;
+            }
+        }
+    }
+    for (int32_t i = 0; i < nout; ++i) {
+        const int m = mask ? (mask[i] != 0) : 1;
+        const int pass = m ^ (complement != 0);
+        const double old = accum ? w[i] : inf;
+        if (pass)
+            w[i] = (accum && old < t[i]) ? old : t[i];
+        else
+            w[i] = old;
+    }
+    free(t);
+    return 0;
+}
+
+/*
+ * Single-source shortest paths as Bellman-Ford in the (min, +) semiring:
+ * d_0 = e_s (0 at s, +inf elsewhere); d_{k+1}(i) = min(d_k(i), min over edges
+ * (j -> i) of fl32(d_k(j) + a(j, i))), i.e. d_{k+1} = min(d_k, A^T d_k), until
+ * d_{k+1} = d_k.  Every sum is rounded to binary32 as it is formed.  For
+ * non-negative weights the fixpoint is, for every i, the smallest binary32
+ * left-to-right rounded sum over the paths from s to i, whatever order the
+ * relaxations run in.  Returns the number of iterations that changed d, or
+ * -2 on allocation failure.
+ */
+int32_t oracle_sssp_bf(int32_t n, const int32_t* row_ptr, const int32_t* col, const float* val, int32_t s,
+                       float* d) {
+    const float inf = 1.0f / 0.0f;
+    float* nd = (float*)malloc((size_t)(n > 0 ? n : 1) * sizeof(float));
+    if (!nd) return -2;
+    for (int32_t i = 0; i < n; ++i) d[i] = inf;
+    d[s] = 0.0f;
+    int32_t iters = 0;
+    for (;;) {
+        int changed = 0;
+        memcpy(nd, d, (size_t)n * sizeof(float));
+        for (int32_t j = 0; j < n; ++j) {
+            if (d[j] == inf) continue;
+            for (int64_t k = row_ptr[j]; k < row_ptr[j + 1]; ++k) {
+                volatile float x = d[j] + val[k]; /* one binary32 rounding */
+                if (x < nd[col[k]]) nd[col[k]] = x;
+            }
+        }
+        for (int32_t i = 0; i < n; ++i)
+            if (nd[i] != d[i]) changed = 1;
+        if (!changed) break;
+        memcpy(d, nd, (size_t)n * sizeof(float));
+        ++iters;
+    }
+    free(nd);
+    return iters;
 }

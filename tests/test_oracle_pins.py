@@ -369,3 +369,138 @@ def test_ms_bfs_lanes_equal_single_sources_including_duplicates():
     # one lane against brute force as an outside check
     adj = dense_adjacency(n, src, dst)
     assert np.array_equal(d[1], brute_force_depth(adj, srcs[1]))
+
+
+# ---------------------------------------------------------------- (min, +) semiring (Section 5.6)
+
+def _weights(m, seed, integer=True):
+    """Seeded weights: integers 1..64 (sums exact in binary32) or floats in (0, 8)."""
+    rng = np.random.default_rng(seed)
+    if integer:
+        return rng.integers(1, 65, size=m).astype(np.float32)
+    return (rng.random(m) * 8.0 + 1e-3).astype(np.float32)
+
+
+@pytest.mark.parametrize("symmetrize", [True, False])
+def test_csr_weights_match_pair_dictionary(symmetrize):
+    n, s, d = synth.er_edges(60, 0.08, seed=21, directed=True)
+    s = np.concatenate([s, s[:40]])  # parallel pairs with other weights
+    d = np.concatenate([d, d[:40]])
+    w = _weights(len(s), 5, integer=False)
+    want = {}
+    for a, b, x in zip(s.tolist(), d.tolist(), w.tolist()):
+        if a == b:
+            continue
+        for r, c in ([(a, b), (b, a)] if symmetrize else [(a, b)]):
+            want[(r, c)] = min(want.get((r, c), np.inf), x)
+    g = oracle.graph_weighted(n, s, d, w, symmetrize=symmetrize)
+    got = {(r, int(g.out_col[k])): float(g.out_val[k]) for r in range(n) for k in range(g.out_ptr[r], g.out_ptr[r + 1])}
+    assert got == want
+    got_t = {(int(g.in_col[k]), r): float(g.in_val[k]) for r in range(n) for k in range(g.in_ptr[r], g.in_ptr[r + 1])}
+    assert got_t == want
+
+
+@pytest.mark.parametrize("transpose,masked,complement,accum",
+                         [(t, m, c, a) for t in (0, 1) for m in (0, 1) for c in (0, 1) for a in (0, 1)])
+def test_minplus_with_zero_weights_is_the_boolean_matvec(transpose, masked, complement, accum):
+    """All weights 0 and u in {0, +inf}: (min, +) reduces to (OR, AND) with 0 = true."""
+    n, s, d = synth.er_edges(50, 0.06, seed=3, directed=True)
+    g = oracle.graph_weighted(n, s, d, np.zeros(len(s), np.float32), symmetrize=False)
+    for k in range(4):
+        ub = synth.vertex_set(n, 0.2, seed=7 + k)
+        mb = synth.vertex_set(n, 0.5, seed=17 + k) if masked else None
+        wb = synth.vertex_set(n, 0.3, seed=27 + k)
+        want = oracle.mxv(n, n, g.out_ptr, g.out_col, ub, mb, transpose=bool(transpose),
+                          complement=bool(complement), accum=bool(accum), w_old=wb)
+        u = np.where(ub != 0, 0.0, np.inf)
+        w_old = np.where(wb != 0, 0.0, np.inf)
+        got = oracle.mxv_minplus(n, n, g.out_ptr, g.out_col, g.out_val, u, mb, transpose=bool(transpose),
+                                 complement=bool(complement), accum=bool(accum), w_old=w_old)
+        assert np.array_equal(got == 0.0, want.astype(bool))
+        assert np.all((got == 0.0) | np.isinf(got))
+
+
+def test_minplus_unit_vector_gives_a_row_of_weights():
+    n, s, d = synth.er_edges(40, 0.1, seed=9, directed=True)
+    g = oracle.graph_weighted(n, s, d, _weights(len(s), 2, integer=False), symmetrize=False)
+    for j in range(n):
+        u = np.full(n, np.inf)
+        u[j] = 0.0
+        got = oracle.mxv_minplus(n, n, g.out_ptr, g.out_col, g.out_val, u, transpose=True)
+        want = np.full(n, np.inf)
+        for k in range(g.out_ptr[j], g.out_ptr[j + 1]):
+            want[g.out_col[k]] = g.out_val[k]  # (A^T e_j)(c) = A(j, c)
+        assert np.array_equal(got, want)
+        got_n = oracle.mxv_minplus(n, n, g.out_ptr, g.out_col, g.out_val, u, transpose=False)
+        want_n = np.full(n, np.inf)
+        for r in range(n):
+            for k in range(g.out_ptr[r], g.out_ptr[r + 1]):
+                if g.out_col[k] == j:
+                    want_n[r] = g.out_val[k]  # (A e_j)(r) = A(r, j)
+        assert np.array_equal(got_n, want_n)
+
+
+def test_minplus_is_tropically_linear():
+    """min-plus matvec distributes over min and commutes with adding a constant."""
+    n, s, d = synth.rmat_edges(7, 8, seed=4)
+    g = oracle.graph_weighted(n, s, d, _weights(len(s), 3))
+    rng = np.random.default_rng(1)
+    for _ in range(5):
+        u1 = np.where(rng.random(n) < 0.3, rng.integers(0, 100, n).astype(np.float64), np.inf)
+        u2 = np.where(rng.random(n) < 0.3, rng.integers(0, 100, n).astype(np.float64), np.inf)
+        f = lambda u: oracle.mxv_minplus(n, n, g.out_ptr, g.out_col, g.out_val, u, transpose=True)
+        assert np.array_equal(f(np.minimum(u1, u2)), np.minimum(f(u1), f(u2)))
+        assert np.array_equal(f(u1 + 5.0), f(u1) + 5.0)
+
+
+def test_sssp_matches_scipy_dijkstra():
+    scipy_sparse = pytest.importorskip("scipy.sparse")
+    csgraph = pytest.importorskip("scipy.sparse.csgraph")
+    for directed, (n, s, d) in [(False, synth.rmat_edges(9, 8, seed=12)),
+                                (True, synth.er_edges(300, 0.01, seed=13, directed=True)),
+                                (False, synth.grid_edges(20, 15, p_delete=0.05, seed=14))]:
+        for integer in (True, False):
+            w = _weights(len(s), 6, integer=integer)
+            g = oracle.graph_weighted(n, s, d, w, symmetrize=not directed)
+            a = scipy_sparse.csr_matrix((g.out_val, g.out_col, g.out_ptr), shape=(n, n))
+            for src in synth.sources(n, s, d, 3, seed=15):
+                got, _ = oracle.sssp(g, int(src))
+                want = csgraph.dijkstra(a, directed=True, indices=int(src))
+                assert np.array_equal(np.isinf(got), np.isinf(want))
+                fin = np.isfinite(want)
+                if integer:  # integer sums below 2^24 are exact in binary32
+                    assert np.array_equal(got[fin].astype(np.float64), want[fin])
+                else:  # each of at most n - 1 additions rounds by at most half an ulp
+                    assert np.all(np.abs(got[fin] - want[fin]) <= want[fin] * (n * 2.0 ** -24) + 1e-30)
+
+
+def test_sssp_unit_weights_give_bfs_depth():
+    n, s, d = synth.rmat_edges(9, 8, seed=31)
+    g = oracle.graph_weighted(n, s, d, np.ones(len(s), np.float32))
+    for src in synth.sources(n, s, d, 4, seed=2):
+        depth, _, _ = oracle.bfs(g, int(src))
+        dist, _ = oracle.sssp(g, int(src))
+        assert np.array_equal(np.where(depth >= 0, depth.astype(np.float32), np.float32(np.inf)), dist)
+
+
+def test_sssp_bellman_optimality_conditions():
+    """d(s) = 0; d(v) <= fl32(d(u) + w) on every edge; every reached v != s has a
+    tight in-edge.  (Checks the float result itself, not how it was computed.)"""
+    n, s, d = synth.rmat_edges(10, 8, seed=33)
+    g = oracle.graph_weighted(n, s, d, _weights(len(s), 8, integer=False))
+    val32 = g.out_val.astype(np.float32)
+    for src in synth.sources(n, s, d, 2, seed=4):
+        dist, _ = oracle.sssp(g, int(src))
+        assert dist[src] == 0.0
+        tight = np.zeros(n, dtype=bool)
+        for u in range(n):
+            if not np.isfinite(dist[u]):
+                continue
+            for k in range(g.out_ptr[u], g.out_ptr[u + 1]):
+                v = g.out_col[k]
+                x = np.float32(dist[u] + val32[k])
+                assert dist[v] <= x
+                tight[v] |= dist[v] == x
+        reached = np.isfinite(dist)
+        reached[src] = False
+        assert np.all(tight[reached])
