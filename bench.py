@@ -61,6 +61,8 @@ def parse():
                    help="masked-mxv operator sweep (RMAT scale 20 and the 2048x2048 grid) instead of the BFS line")
     p.add_argument("--ablation", action="store_true",
                    help="Table 2 ladder and per-level push/pull costs on RMAT scale 21 (edge factor 48)")
+    p.add_argument("--sssp", action="store_true",
+                   help="direction-optimised Bellman-Ford SSSP over the (min, +) semiring on RMAT scale 22")
     p.add_argument("--probe", type=int, default=None, metavar="K",
                    help="profiling aid: run only source K of the workload --repeat times (for ncu -k bfs_kernel); "
                         "K = -1: source 0 --repeat times, then each workload source once")
@@ -393,6 +395,89 @@ def run_ablation(args):
            "graph": {"name": "rmat21-ef48", "vertices": n, "stored_edges": int(nnz), "sources": len(srcs)},
            "ladder": rows, "tuned_descriptor": gbx.desc_dict(tuned), "per_level": levels,
            "paper_table2_k40c_gteps": [0.874, 1.411, 1.527, 3.932, 15.83, 42.44]}
+    print(json.dumps(out), flush=True)
+    g.free()
+
+
+def sssp_bytes(tr, n: int) -> int:
+    """Algorithmic bytes of one SSSP from its iteration trace: push iterations read
+    12 B per queued vertex (id, prefix, row start), 12 B per relaxed edge (column,
+    weight, distance of the target) and write 16 B per improved vertex (distance,
+    stamp, queue slot and prefix); pull iterations read every row's two offsets
+    (8 B) plus 12 B per in-edge and write the n/8-byte improved-set bitmap and the
+    improved distances; the initialisation writes distances and stamps (8n)."""
+    total = 8 * n
+    for r in tr:
+        if r["direction"] == 1:  # push
+            total += 12 * int(r["nf"]) + 12 * int(r["e_exam"]) + 16 * int(r["n_new"])
+        else:
+            total += 8 * n + 12 * int(r["e_exam"]) + n // 8 + 4 * int(r["n_new"])
+    return total
+
+
+def run_sssp(args):
+    """SSSP over the (min, +) semiring (Section 5.6): RMAT scale 22, edge factor 16,
+    seeded integer weights 1..64 (sums exact in binary32), 16 sources; the
+    direction rule (3 phases), beta = 0 (the two phases of Section 5.6), push only
+    and pull only.  Rate = relaxed edges (trace) / time; bytes from the trace."""
+    import torch
+
+    import synth
+    from paper_1804_03327_gb300 import gbx
+
+    peak, peak_kind = peaks()
+    n, src, dst = synth.rmat_edges(args.scale, EDGE_FACTOR, seed=SEED)
+    rng = np.random.default_rng(SEED)
+    w = rng.integers(1, 65, size=len(src)).astype(np.float32)
+    g = gbx.graph_build(n, src, dst)
+    gbx.graph_set_weights(g, src, dst, w)
+    _, nnz, _ = g.info()
+    srcs = [int(x) for x in synth.sources(n, src, dst, 16, seed=SEED + 7)]
+    dist = torch.empty(n, dtype=torch.float32, device="cuda")
+    rows = []
+    modes = [("auto (alpha 0.01, beta 0.01)", gbx.desc_init()), ("two-phase (beta 0)", gbx.desc_init(beta=0.0)),
+             ("push only", gbx.desc_init(direction=gbx.DIR_PUSH)), ("pull only", gbx.desc_init(direction=gbx.DIR_PULL))]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for label, desc in modes:
+        relaxed, its, byts, sched = 0, 0, 0, None
+        for x in srcs:
+            d = gbx.Desc.from_buffer_copy(desc)
+            d.trace = 1
+            gbx.sssp(g, x, dist, d)
+            tr = gbx.sssp_trace(g)
+            relaxed += int(tr["e_exam"].sum())
+            its += len(tr)
+            byts += sssp_bytes(tr, n)
+            if sched is None:
+                sched = "".join("P" if r == gbx.DIR_PUSH else "L" for r in tr["direction"])
+        for x in srcs[:3]:
+            gbx.sssp(g, x, dist, desc)
+        torch.cuda.synchronize()
+        e0.record()
+        for x in srcs:
+            gbx.sssp(g, x, dist, desc)
+        e1.record()
+        torch.cuda.synchronize()
+        gbx.graph_sync(g)
+        t = e0.elapsed_time(e1) / 1e3
+        rows.append({"mode": label, "ms_per_sssp": t * 1e3 / len(srcs), "iterations_mean": its / len(srcs),
+                     "relaxed_edges_per_s": relaxed / t, "achieved_gbs": byts / t / 1e9,
+                     "roofline_frac": byts / t / 1e9 / peak, "schedule_first_source": sched})
+    # CPU oracle (binary32 Bellman-Ford, one source) as the reported baseline
+    import oracle
+    og = oracle.graph_weighted(n, src, dst, w)
+    t0 = time.time()
+    od, oit = oracle.sssp(og, srcs[0])
+    tc = time.time() - t0
+    gbx.sssp(g, srcs[0], dist, gbx.desc_init())
+    same = bool(np.array_equal(dist.cpu().numpy(), od))
+    out = {"metric": "SSSP time and relaxed-edge rate, (min, +) Bellman-Ford", "unit": "ms",
+           "graph": {"name": f"rmat{args.scale}-ef16", "vertices": n, "stored_edges": int(nnz),
+                     "weights": "seeded integers 1..64"},
+           "sources": len(srcs), "peak": peak, "peak_kind": peak_kind, "rows": rows,
+           "cpu_baseline": {"ms_per_sssp": tc * 1e3, "iterations": oit, "cores": 1, "kind": "oracle",
+                            "sample": "first source, Jacobi Bellman-Ford in binary32"},
+           "first_source_equals_oracle": same}
     print(json.dumps(out), flush=True)
     g.free()
 
@@ -790,6 +875,8 @@ def main():
         run_sweep(args)
     elif args.ablation:
         run_ablation(args)
+    elif args.sssp:
+        run_sssp(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

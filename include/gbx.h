@@ -98,6 +98,27 @@ gbx_status gbx_graph_info(const gbx_graph* g, int32_t* n, int64_t* nnz, int32_t*
  * until gbx_graph_free. */
 gbx_status gbx_graph_csr(const gbx_graph* g, int32_t transpose, const int32_t** row_ptr, const int32_t** col);
 
+/*
+ * Attach binary32 edge weights for the (min, +) semiring (Section 5.6; the
+ * Boolean path of Section 5.5 needs none).  (src[e], dst[e], w[e]) for e < m
+ * must be the edge list the graph was built from: w[e] goes to the stored
+ * entry of that pair, and to its reverse when the graph was symmetrised;
+ * parallel pairs keep the smallest weight; self-loops are skipped when the
+ * build dropped them.  Host arrays, or device arrays with GBX_DEVICE_EDGES in
+ * flags.  Weights must be finite.  Calling again replaces all weights (entries
+ * no pair reaches get +inf).  Synchronous.  Errors: NULL_POINTER,
+ * INVALID_INDEX (vertex outside [0, n) or a weight that is not finite),
+ * INVALID_VALUE (a pair the graph does not store, unknown flags; the weights
+ * are then unspecified), OUT_OF_MEMORY, CUDA.
+ */
+gbx_status gbx_graph_set_weights(gbx_graph* g, int64_t m, const int32_t* src, const int32_t* dst, const float* w,
+                                 uint32_t flags, void* stream);
+
+/* Copy the edge weights of A (transpose = 0: aligned with the CSR of A) or A^T
+ * (transpose = 1: aligned with the CSR of A^T) into dst (float[nnz], host or
+ * device).  Synchronous.  Errors: NULL_POINTER, INVALID_VALUE (no weights). */
+gbx_status gbx_graph_copy_weights(const gbx_graph* g, int32_t transpose, float* dst);
+
 /* Copy the CSR arrays of A (transpose = 0) or A^T (transpose = 1) into
  * caller buffers row_ptr_dst (int32[n + 1]) and col_dst (int32[nnz]), each
  * host or device memory.  Synchronous. */
@@ -115,6 +136,8 @@ gbx_status gbx_graph_sync(gbx_graph* g, void* stream);
 #define GBX_DENSE 0  /* data: uint8_t[size], entry i is true iff data[i] != 0 */
 #define GBX_SPARSE 1 /* data: int32_t[capacity] indices, ascending and unique (Section 3);
                         *nnz (a device int32) holds how many are stored */
+#define GBX_DENSE_F32 2 /* data: float[size], the values of the (min, +) semiring; +inf marks
+                           an absent entry (the semiring's identity) */
 
 /* A non-owning view of a vector in device memory. */
 typedef struct {
@@ -173,6 +196,9 @@ void gbx_desc_init(gbx_desc* d);
 /* ------------------------------------------------------------------ matvec */
 
 #define GBX_LOR_LAND 0 /* Boolean semiring ({0,1}, OR, AND, 0) of Algorithm 1 */
+#define GBX_MIN_PLUS_F32 1 /* tropical semiring (R u {+inf}, +, min, +inf) over binary32, the one
+                              Section 5.6 names for SSSP; needs edge weights (gbx_graph_set_weights)
+                              and GBX_DENSE_F32 u and w */
 
 /*
  * w = (A u) .* mask  (or A^T u with desc->transpose), over `semiring`.
@@ -189,6 +215,16 @@ void gbx_desc_init(gbx_desc* d);
  * must have size == n.  w must not alias u or mask.  Asynchronous on `stream`.
  * Errors: NULL_POINTER, NOT_SUPPORTED (semiring), DIMENSION_MISMATCH,
  * INVALID_VALUE (format, capacity < size for a SPARSE output, desc fields).
+ *
+ * With semiring GBX_MIN_PLUS_F32 (Section 4's generalised semiring, Section
+ * 5.6): t(i) = min over entries (i, j) of A' of (A'(i, j) + u(j)), +inf if none;
+ * w(i) = pass(i) ? (accum ? min(w_old(i), t(i)) : t(i)) : (accum ? w_old(i) :
+ * +inf).  u and w are GBX_DENSE_F32, the mask stays Boolean (DENSE or SPARSE);
+ * every sum is one binary32 addition, so w equals the exact result rounded
+ * to binary32.  early_exit is ignored (it exists for Boolean semirings only,
+ * Section 5.6) and push_sort must be 0 (NOT_SUPPORTED).  PUSH folds u's finite
+ * entries' columns into w with atomic minima; PULL computes each passing row.
+ * The graph must have weights (INVALID_VALUE otherwise).
  */
 gbx_status gbx_mxv(gbx_vector* w, const gbx_vector* mask, int32_t semiring, const gbx_graph* A,
                    const gbx_vector* u, const gbx_desc* desc, void* stream);
@@ -278,6 +314,31 @@ typedef struct {
 /* Copy the trace of the last traced BFS on g into levels[0..cap) and its
  * length into *nlevels.  Synchronises the graph's last BFS stream. */
 gbx_status gbx_bfs_trace(gbx_graph* g, gbx_level* levels, int32_t cap, int32_t* nlevels);
+
+/*
+ * Single-source shortest paths over the edge weights (gbx_graph_set_weights),
+ * the direction-optimised Bellman-Ford that Section 5.6 sketches for the
+ * (min, +) semiring: d <- min(d, A^T d) restricted, while it is small, to the
+ * columns of the vertices whose distance improved in the last iteration (push,
+ * Eq 5 with atomic minima), and over every row once that set is large (pull,
+ * Eq 2 without mask or early exit).  The switch uses Section 6.3's rule on the
+ * improved-set size (desc->alpha up, desc->beta down; beta = 0 keeps the two
+ * phases of Section 5.6); desc->direction PUSH or PULL forces one.  dist is a
+ * device float[n]: dist[source] = 0, +inf where unreachable.  Every relaxation
+ * is one binary32 addition; for non-negative weights the result is, per vertex,
+ * the smallest left-to-right rounded path sum, independent of the schedule.
+ * A negative cycle ends in GBX_ERR_OVERFLOW after n iterations (reported by
+ * gbx_graph_sync).  One persistent cooperative launch, asynchronous on
+ * `stream`.  Errors: NULL_POINTER, INVALID_INDEX, INVALID_VALUE (no weights,
+ * desc fields), NOT_SUPPORTED (push_sort), CUDA.
+ */
+gbx_status gbx_sssp(gbx_graph* g, int32_t source, float* dist, const gbx_desc* desc, void* stream);
+
+/* Per-iteration records of the last traced gbx_sssp on g (synchronises): direction,
+ * iteration, nf = vertices improved by the previous iteration (1 for the first),
+ * mf = their out-edges (push iterations; -1 on pull), e_exam = edges relaxed,
+ * n_new = vertices improved, mf_new, time_ns; nu, nu_nz and mu are -1. */
+gbx_status gbx_sssp_trace(gbx_graph* g, gbx_level* levels, int32_t cap, int32_t* nlevels);
 
 /* Depth element types of gbx_bfs_batch. */
 #define GBX_DEPTH_I32 0

@@ -224,8 +224,8 @@ int oracle_mxv(int32_t nrows, int32_t ncols, const int32_t* row_ptr, const int32
 /*
  * Weights of the CSR (row_ptr, col) built by oracle_csr_build from the same edge
  * list: val[k] = the smallest w[e] over input pairs e that map to entry k (the
- * pair itself, and its reverse when symmetrising).  Entries are located by a
- * linear scan of the row (rows are sorted; this is the slow, plain way).
+ * pair itself, and its reverse when symmetrising).  Entries are located by
+ * binary search in the row (rows are sorted ascending).
  * Returns 0, or -1 if a pair has no entry (the CSR was not built from this list).
  */
 int oracle_csr_weights(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, const float* w,
@@ -238,12 +238,18 @@ int oracle_csr_weights(int32_t n, int64_t m, const int32_t* src, const int32_t* 
         for (int dir = 0; dir < (symmetrize ? 2 : 1); ++dir) {
             const int32_t r = dir ? dst[e] : src[e];
             const int32_t c = dir ? src[e] : dst[e];
-            int64_t at = -1;
-            for (int64_t k = row_ptr[r]; k < row_ptr[r + 1]; ++k)
-                if (col[k] == c) {
-                    at = k;
+            int64_t lo = row_ptr[r], hi = row_ptr[r + 1], at = -1;
+            while (lo < hi) {
+                const int64_t mid = lo + (hi - lo) / 2;
+                if (col[mid] == c) {
+                    at = mid;
                     break;
                 }
+                if (col[mid] < c)
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
             if (at < 0) return -1;
             if ((double)w[e] < val[at]) val[at] = (double)w[e];
         }

@@ -133,10 +133,12 @@ __device__ __forceinline__ int32_t warp_find_entry(const int32_t* qp, int32_t co
     return lo;
 }
 
-// Edges of one push step: the frontier vertex u and child v of each lane's edges.
+// Edges of one push step: the frontier vertex u, child v and CSR position k
+// (for edge values) of each lane's edges.
 struct PushStep {
     int32_t u[kPushIlp];
     int32_t v[kPushIlp];
+    int32_t k[kPushIlp];
 };
 
 // Walks a warp's edge range: maps edge ids to (queue entry, child) with a window
@@ -180,9 +182,11 @@ struct PushCursor {
             const int32_t e = base + 32 * t + lane;
             st.u[t] = -1;
             st.v[t] = 0;
+            st.k[t] = 0;
             if (e < e1) {
                 st.u[t] = q[kk];
-                st.v[t] = __ldg(out_col + (e + qd[kk]));
+                st.k[t] = e + qd[kk];
+                st.v[t] = __ldg(out_col + st.k[t]);
             }
         }
         k += (int32_t)before;

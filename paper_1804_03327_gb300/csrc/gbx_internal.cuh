@@ -131,6 +131,11 @@ struct Graph {
     // pull row reads this dense array instead of a random sector of in_col
     int32_t* first_in = nullptr;
     int32_t* first_out = nullptr;
+    // binary32 edge weights (gbx_graph_set_weights): out_val[k] belongs to out_col[k],
+    // in_val[k] to in_col[k] (aliases out_val when symmetric); NULL until set
+    float* out_val = nullptr;
+    float* in_val = nullptr;
+    int32_t drop_self_loops = 0;  // as built
     Workspace ws;  // scratch of the operations called on this graph (ordered on one stream)
     // host-side copies for gbx_bfs_host (allocated on first use)
     int32_t* hdepth[2] = {nullptr, nullptr};
@@ -203,6 +208,15 @@ __device__ __forceinline__ int ld_volatile_i32(const int32_t* p) { return *(cons
 
 __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
     return *(const volatile unsigned long long*)p;
+}
+
+// atomic min of a binary32 value: non-negative floats order like their int bits
+// and negative ones in reverse of their unsigned bits, so the two halves use
+// atomicMin (int) and atomicMax (unsigned).  Returns the previous value.  NaN is
+// never stored (callers keep it out).
+__device__ __forceinline__ float atomic_min_f32(float* a, float v) {
+    if (v >= 0.0f) return __int_as_float(atomicMin(reinterpret_cast<int*>(a), __float_as_int(v)));
+    return __uint_as_float(atomicMax(reinterpret_cast<unsigned int*>(a), __float_as_uint(v)));
 }
 
 __device__ __forceinline__ uint32_t lanemask_lt() {

@@ -179,6 +179,8 @@ static void graph_release(Graph* g) {
     if (g->nz_out != g->nz_in) f(g->nz_out);
     if (g->first_out != g->first_in) f(g->first_out);
     f(g->first_in);
+    if (g->in_val != g->out_val) f(g->in_val);
+    f(g->out_val);
     workspace_release(g->ws);
     for (int i = 0; i < 2; ++i) {
         f(g->hdepth[i]);
@@ -222,6 +224,7 @@ static gbx_status build_impl(Graph* g, int32_t n, int64_t m, const int32_t* src,
     g->n = n;
     g->nwords = (n + 31) / 32;
     g->symmetric = sym;
+    g->drop_self_loops = drop;
     GBX_TRY(workspace_alloc(g->ws, n));
 
     const int64_t K = sym ? 2 * m : m;

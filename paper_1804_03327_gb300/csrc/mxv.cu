@@ -339,7 +339,7 @@ __global__ void set_push_stats_kernel(MxvStats* s, int32_t ucount, int64_t edges
 }
 
 static gbx_status check_vec(const gbx_vector* v, int32_t n, const char* name, bool output) {
-    GBX_CHECK(v->format == GBX_DENSE || v->format == GBX_SPARSE, GBX_ERR_INVALID_VALUE,
+    GBX_CHECK(v->format == GBX_DENSE || v->format == GBX_SPARSE || v->format == GBX_DENSE_F32, GBX_ERR_INVALID_VALUE,
               std::string(name) + ": unknown format");
     GBX_CHECK(v->size == n, GBX_ERR_DIMENSION_MISMATCH, std::string(name) + ": size differs from the graph's n");
     GBX_CHECK(v->data != nullptr, GBX_ERR_NULL_POINTER, std::string(name) + ": data is NULL");
@@ -353,6 +353,31 @@ static gbx_status check_vec(const gbx_vector* v, int32_t n, const char* name, bo
     return GBX_OK;
 }
 
+// mask -> bitmap of passing rows; pass = m XOR complement (Algorithm 2, line 3).
+// No mask: every row passes (*pass_bm = NULL), or none with the complement.
+static gbx_status build_pass(Graph* G, const gbx_vector* mask, int complement, const uint32_t** pass_bm,
+                             bool* nothing_passes, cudaStream_t s) {
+    const int32_t n = G->n;
+    uint32_t* pass = G->ws.bm[1];
+    *pass_bm = nullptr;
+    *nothing_passes = false;
+    if (!mask) {
+        *nothing_passes = complement != 0;
+    } else if (mask->format == GBX_DENSE) {
+        GBX_TRY(pack_dense_to_bitmap((const uint8_t*)mask->data, n, complement ? 1u : 0u, pass, s));
+        *pass_bm = pass;
+    } else {
+        GBX_TRY(fill_bitmap(pass, n, 0u, s));
+        GBX_TRY(scatter_list_to_bitmap((const int32_t*)mask->data, mask->nnz, mask->capacity, n, pass, s));
+        if (complement) GBX_TRY(invert_bitmap(pass, n, s));
+        *pass_bm = pass;
+    }
+    return GBX_OK;
+}
+
+gbx_status mxv_minplus(Graph* G, float* w, const uint32_t* pass_bm, bool nothing_passes, const float* u,
+                       const gbx_desc& d, cudaStream_t s);
+
 }  // namespace gbx
 
 using namespace gbx;
@@ -362,7 +387,8 @@ extern "C" gbx_status gbx_mxv(gbx_vector* w, const gbx_vector* mask, int32_t sem
     clear_error();
     GBX_TRY(check_graph(A));
     GBX_CHECK(w != nullptr && u != nullptr, GBX_ERR_NULL_POINTER, "w or u is NULL");
-    GBX_CHECK(semiring == GBX_LOR_LAND, GBX_ERR_NOT_SUPPORTED, "only the Boolean semiring GBX_LOR_LAND is supported");
+    GBX_CHECK(semiring == GBX_LOR_LAND || semiring == GBX_MIN_PLUS_F32, GBX_ERR_NOT_SUPPORTED,
+              "semiring must be GBX_LOR_LAND or GBX_MIN_PLUS_F32");
     Graph* G = const_cast<Graph*>(as_impl(A));
     const int32_t n = G->n;
     GBX_TRY(check_vec(u, n, "u", false));
@@ -379,7 +405,21 @@ extern "C" gbx_status gbx_mxv(gbx_vector* w, const gbx_vector* mask, int32_t sem
     GBX_CHECK(d.alpha >= 0.0f && d.alpha == d.alpha, GBX_ERR_INVALID_VALUE, "desc.alpha must be >= 0");
     GBX_CHECK(d.push_sort == 0 || d.push_sort == 1, GBX_ERR_INVALID_VALUE, "desc.push_sort must be 0 or 1");
     for (int k = 0; k < 2; ++k) GBX_CHECK(d.reserved[k] == 0, GBX_ERR_INVALID_VALUE, "desc.reserved must be 0");
+    GBX_CHECK(!mask || mask->format != GBX_DENSE_F32, GBX_ERR_INVALID_VALUE, "mask: GBX_DENSE or GBX_SPARSE");
     cudaStream_t s = (cudaStream_t)stream;
+    if (semiring == GBX_MIN_PLUS_F32) {
+        GBX_CHECK(u->format == GBX_DENSE_F32 && w->format == GBX_DENSE_F32, GBX_ERR_INVALID_VALUE,
+                  "the (min, +) semiring takes GBX_DENSE_F32 u and w");
+        GBX_CHECK(d.push_sort == 0, GBX_ERR_NOT_SUPPORTED, "desc.push_sort is for the Boolean semiring");
+        const uint32_t* pbm = nullptr;
+        bool none = false;
+        GBX_TRY(build_pass(G, mask, d.mask_complement, &pbm, &none, s));
+        GBX_TRY(mxv_minplus(G, (float*)w->data, pbm, none, (const float*)u->data, d, s));
+        G->ws.last_stream = s;
+        return GBX_OK;
+    }
+    GBX_CHECK(u->format != GBX_DENSE_F32 && w->format != GBX_DENSE_F32, GBX_ERR_INVALID_VALUE,
+              "GBX_DENSE_F32 vectors belong to the (min, +) semiring");
 
     // w = A' u with A' = A^T (transpose) or A.  Pull reads rows of A' (CSR of A'),
     // push reads the columns of A' selected by u, i.e. rows of (A')^T.
@@ -391,7 +431,6 @@ extern "C" gbx_status gbx_mxv(gbx_vector* w, const gbx_vector* mask, int32_t sem
     const int32_t* push_col = d.transpose ? G->out_col : G->in_col;
 
     uint32_t* ubm = G->ws.bm[0];
-    uint32_t* pass = G->ws.bm[1];
     uint32_t* R = G->ws.bm[2];
     int32_t* list_count = G->ws.flag + 0;
     int32_t* dflag = G->ws.flag + 1;
@@ -422,20 +461,9 @@ extern "C" gbx_status gbx_mxv(gbx_vector* w, const gbx_vector* mask, int32_t sem
             GBX_TRY(scatter_list_to_bitmap(ulist, ucount, ucap, n, ubm, s));
         }
     }
-    // mask -> bitmap of passing rows; pass = m XOR complement (Algorithm 2, line 3)
     const uint32_t* pass_bm = nullptr;
     bool nothing_passes = false;
-    if (!mask) {
-        nothing_passes = d.mask_complement != 0;
-    } else if (mask->format == GBX_DENSE) {
-        GBX_TRY(pack_dense_to_bitmap((const uint8_t*)mask->data, n, d.mask_complement ? 1u : 0u, pass, s));
-        pass_bm = pass;
-    } else {
-        GBX_TRY(fill_bitmap(pass, n, 0u, s));
-        GBX_TRY(scatter_list_to_bitmap((const int32_t*)mask->data, mask->nnz, mask->capacity, n, pass, s));
-        if (d.mask_complement) GBX_TRY(invert_bitmap(pass, n, s));
-        pass_bm = pass;
-    }
+    GBX_TRY(build_pass(G, mask, d.mask_complement, &pass_bm, &nothing_passes, s));
     // Algorithm 3 (desc.push_sort): sizes its scratch from the frontier, so the
     // frontier size and the AUTO decision are taken on the host
     bool sorted_done = false;

@@ -37,12 +37,14 @@ DROP_SELF_LOOPS = 0x2
 DEVICE_EDGES = 0x4
 DENSE = 0
 SPARSE = 1
+DENSE_F32 = 2
 DIR_AUTO = 0
 DIR_PUSH = 1
 DIR_PULL = 2
 HEUR_RATIO = 0
 HEUR_BEAMER = 1
 LOR_LAND = 0
+MIN_PLUS_F32 = 1
 DEPTH_I32 = 0
 DEPTH_I16 = 1
 TUNE_BFS = 0
@@ -55,6 +57,7 @@ EXPORTED = [
     "gbx_mxv_pull_noalloc", "gbx_bfs_batch", "gbx_bfs_batch_trace",
     "gbx_server_config_init", "gbx_server_create", "gbx_server_add_graph", "gbx_server_graph_lanes",
     "gbx_server_submit", "gbx_server_poll", "gbx_server_stats", "gbx_server_destroy", "gbx_autotune",
+    "gbx_graph_set_weights", "gbx_graph_copy_weights", "gbx_sssp", "gbx_sssp_trace",
 ]
 
 
@@ -148,6 +151,10 @@ def load():
                 "gbx_server_destroy": (ctypes.c_int, [p]),
                 "gbx_autotune": (ctypes.c_int, [p, i32, p, i32, ctypes.POINTER(Desc), ctypes.POINTER(ctypes.c_double),
                                                 ctypes.c_char_p, p]),
+                "gbx_graph_set_weights": (ctypes.c_int, [p, i64, p, p, p, u32, p]),
+                "gbx_graph_copy_weights": (ctypes.c_int, [p, i32, p]),
+                "gbx_sssp": (ctypes.c_int, [p, i32, p, ctypes.POINTER(Desc), p]),
+                "gbx_sssp_trace": (ctypes.c_int, [p, ctypes.POINTER(Level), i32, ctypes.POINTER(i32)]),
             }
             for name, (res, args) in sigs.items():
                 fn = getattr(L, name)
@@ -278,6 +285,44 @@ def dense(t) -> Vector:
     """View of a CUDA uint8 tensor as a GBX_DENSE vector."""
     assert t.is_cuda and str(t.dtype) == "torch.uint8" and t.is_contiguous()
     return Vector(DENSE, t.numel(), t.data_ptr(), None, 0)
+
+
+def dense_f32(t) -> Vector:
+    """View of a CUDA float32 tensor as a GBX_DENSE_F32 vector (+inf = no entry)."""
+    assert t.is_cuda and str(t.dtype) == "torch.float32" and t.is_contiguous()
+    return Vector(DENSE_F32, t.numel(), t.data_ptr(), None, 0)
+
+
+def graph_set_weights(g: "Graph", src, dst, w, stream=None):
+    """Attach float32 weights: host numpy arrays or CUDA tensors, the edge list g was built from."""
+    if isinstance(src, np.ndarray):
+        src = np.ascontiguousarray(src, dtype=np.int32)
+        dst = np.ascontiguousarray(dst, dtype=np.int32)
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        ptrs, flags, m = (src.ctypes.data, dst.ctypes.data, w.ctypes.data), 0, len(src)
+    else:
+        src, dst, w = src.contiguous(), dst.contiguous(), w.contiguous()
+        ptrs, flags, m = (src.data_ptr(), dst.data_ptr(), w.data_ptr()), DEVICE_EDGES, src.numel()
+    _check(load().gbx_graph_set_weights(g.handle, int(m), *ptrs, flags, _stream_ptr(stream) if _torch_cuda() else None),
+           "gbx_graph_set_weights")
+
+
+def graph_weights(g: "Graph", transpose: bool = False) -> np.ndarray:
+    _, nnz, _ = g.info()
+    out = np.empty(max(1, nnz), dtype=np.float32)
+    _check(load().gbx_graph_copy_weights(g.handle, int(transpose), out.ctypes.data), "gbx_graph_copy_weights")
+    return out[:nnz]
+
+
+def sssp(g: "Graph", source: int, dist, desc: Desc | None = None, stream=None):
+    """Shortest-path distances from `source` into a CUDA float32 tensor dist[n]."""
+    assert dist.is_cuda and str(dist.dtype) == "torch.float32"
+    _check(load().gbx_sssp(g.handle, int(source), dist.data_ptr(), ctypes.byref(desc) if desc is not None else None,
+                           _stream_ptr(stream)), "gbx_sssp")
+
+
+def sssp_trace(g: "Graph", cap: int = 1 << 16) -> np.ndarray:
+    return _levels(g, cap, "gbx_sssp_trace")
 
 
 def sparse(indices, nnz, size: int) -> Vector:
