@@ -98,9 +98,8 @@ struct Workspace {
     int32_t* flag = nullptr;                                  // small device scratch (mxv decisions)
     unsigned int bar_parity = 0;  // counter of GridBar the next persistent launch uses
     // batched multi-source BFS scratch (allocated on first use, grown as needed)
-    unsigned long long* msV = nullptr;  // visited lanes [n][W]
-    unsigned long long* msF = nullptr;  // lanes found at the current level [n][W]
-    unsigned long long* msN = nullptr;  // push accumulation [n][W]
+    unsigned long long* msV = nullptr;                     // visited lanes [n][W]
+    unsigned long long* msF[3] = {nullptr, nullptr, nullptr};  // lanes found per level, rotating [n][W]
     int64_t ms_cap_words = 0;
     int32_t* ms_src = nullptr;  // device copy of the sources
     int32_t* ms_src_pinned = nullptr;

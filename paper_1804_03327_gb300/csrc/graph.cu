@@ -158,8 +158,7 @@ void workspace_release(Workspace& w) {
     f(w.status);
     f(w.flag);
     f(w.msV);
-    f(w.msF);
-    f(w.msN);
+    for (auto& p : w.msF) f(p);
     f(w.ms_src);
     if (w.ms_src_pinned) cudaFreeHost(w.ms_src_pinned);
     if (w.ms_src_ready) cudaEventDestroy(w.ms_src_ready);

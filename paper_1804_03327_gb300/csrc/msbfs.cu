@@ -4,15 +4,18 @@
 // bit b % 64 of word b / 64 of v's W-word row.
 //
 // State (vertex-major, W words per vertex, W padded to a multiple of the chunk):
-//   V[v]  lanes in which v has been visited,
-//   F[v]  lanes in which v was found at the previous level (valid for vertices on
-//         the active list),
-//   N[v]  push accumulator (zero outside the level's touched vertices),
-//   D     one bit per vertex: every lane visited (pull skips it without loads).
+//   V[v]      lanes in which v has been visited,
+//   F_k[v]    lanes in which v was found at level L (k = L mod 3): level L reads
+//             F_{L mod 3} of its active list, writes F_{(L+1) mod 3}, and clears
+//             F_{(L+2) mod 3} for the list of level L - 1 (read one level earlier,
+//             written again one level later), so no extra barrier is needed;
+//   D         one bit per vertex: every lane visited (pull skips it without loads);
+//   T_k       one bit per vertex: listed for level L + 1 (W > 1), rotating like F.
 // Each level runs in the direction chosen for the whole batch:
 //   push (Eq 5 lane-wise): the active list's edges are split evenly over warps;
-//     each edge ORs F[u] into N[v] (64-bit atomics, only nonzero words); the
-//     vertices touched first are listed, then finalised: new = N & ~V.
+//     each edge claims the lanes F[u] & ~V[v] with a 64-bit atomicOr on V[v];
+//     the lanes it gained are new (unique claimant): their depth is written, they
+//     are ORed into F_next[v], and the first claimant of v lists it.
 //   pull (Eq 4 lane-wise, masking + early exit + operand reuse): every vertex with
 //     an unvisited lane ORs V of its in-neighbours (V is the state before this
 //     level) and stops as soon as every unvisited lane is covered; new = acc & ~V.
@@ -35,16 +38,14 @@ struct MsArgs {
     const int32_t* in_col;
     const uint32_t* nz_in;
     unsigned long long* V;
-    unsigned long long* F;
-    unsigned long long* N;
-    uint32_t* D;        // all lanes visited
-    uint32_t* T;        // touched by the current push level
-    int32_t* tlist;     // touched vertices
+    unsigned long long* Fb[3];  // rotating found-lane buffers
+    uint32_t* D;                // all lanes visited
+    uint32_t* Tb[3];            // rotating "listed" bitmaps
     void* depth;        // [S][n], used when rows is NULL
     void* const* rows;  // optional: lane b writes its n depths to rows[b]
     int depth16;
     const int32_t* src;
-    int32_t* q[2];
+    int32_t* ids[3];  // active lists, rotating like Fb
     int32_t* qp[2];
     int32_t* qd[2];
     LevelCtr* ctr;
@@ -102,7 +103,7 @@ __device__ __forceinline__ void write_depth_word(const MsArgs& a, int32_t w, uns
 // ---------------------------------------------------------------- pull level
 
 template <int CW>
-__device__ __forceinline__ void ms_pull(const MsArgs& a, int32_t L, Stage& st, Acc& acc) {
+__device__ __forceinline__ void ms_pull(const MsArgs& a, int32_t L, unsigned long long* Fn, Stage& st, Acc& acc) {
     const int lane = threadIdx.x & 31;
     const int gwarp = (int)((blockIdx.x * kMsThreads + threadIdx.x) >> 5);
     const int nwarps = (int)((gridDim.x * kMsThreads) >> 5);
@@ -197,7 +198,7 @@ __device__ __forceinline__ void ms_pull(const MsArgs& a, int32_t L, Stage& st, A
 #pragma unroll
             for (int j = 0; j < CW; ++j) {
                 const unsigned long long nw = accw[j] & unv[j];
-                if (mine) a.F[(size_t)v * a.W + c + j] = nw;
+                if (mine) Fn[(size_t)v * a.W + c + j] = nw;
                 if (sink) {
                     a.V[(size_t)v * a.W + c + j] |= nw;
                     full &= unv[j] == nw;
@@ -215,14 +216,15 @@ __device__ __forceinline__ void ms_pull(const MsArgs& a, int32_t L, Stage& st, A
 
 // V |= F for the vertices found by the pull level; mark vertices with all lanes visited.
 template <int CW>
-__device__ __forceinline__ void ms_pull_commit(const MsArgs& a, const int32_t* list, uint32_t count) {
+__device__ __forceinline__ void ms_pull_commit(const MsArgs& a, const int32_t* list, uint32_t count,
+                                               const unsigned long long* Fn) {
     const long long gtid = (long long)blockIdx.x * kMsThreads + threadIdx.x;
     const long long gstride = (long long)gridDim.x * kMsThreads;
     for (long long k = gtid; k < count; k += gstride) {
         const int32_t v = list[k];
         bool full = true;
         for (int32_t w = 0; w < a.W; ++w) {
-            const unsigned long long x = a.V[(size_t)v * a.W + w] | a.F[(size_t)v * a.W + w];
+            const unsigned long long x = a.V[(size_t)v * a.W + w] | Fn[(size_t)v * a.W + w];
             a.V[(size_t)v * a.W + w] = x;
             full &= (x & lane_mask(a.S, w)) == lane_mask(a.S, w);
         }
@@ -232,16 +234,21 @@ __device__ __forceinline__ void ms_pull_commit(const MsArgs& a, const int32_t* l
 
 // ---------------------------------------------------------------- push level
 
+// One phase: each edge (u, v) of the active list claims the lanes F_cur[u] & ~V[v]
+// with an atomicOr on V[v]; the lanes it gained (not set before) are new at level
+// L + 1 and this edge is their only claimant, so it writes their depth and ORs them
+// into F_next[v]; the first edge to gain anything at v lists v (for W == 1 the
+// previous F_next word tells, otherwise the T_next bit).  The plain probe of V[v]
+// only saves atomics (bits are only ever set), the atomic decides.
 template <int CW>
-__device__ __forceinline__ void ms_push_scatter(const MsArgs& a, int cur, uint32_t qcount, uint32_t qedges,
-                                                LevelCtr* cout) {
-    const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void ms_push(const MsArgs& a, int32_t L, const int32_t* q, const int32_t* qp,
+                                        const int32_t* qd, uint32_t qcount, uint32_t qedges,
+                                        const unsigned long long* Fc, unsigned long long* Fn, uint32_t* Tn, Stage& st,
+                                        Acc& acc) {
     const int gwarp = (int)((blockIdx.x * kMsThreads + threadIdx.x) >> 5);
     const int nwarps = (int)((gridDim.x * kMsThreads) >> 5);
-    const int32_t* q = a.q[cur];
-    const int32_t* qp = a.qp[cur];
-    const int32_t* qd = a.qd[cur];
     const int32_t E = (int32_t)qedges;
+    const unsigned long long full0 = lane_mask(a.S, 0);
     int32_t chunk = (int32_t)(((long long)E + nwarps - 1) / nwarps);
     chunk = chunk < kPushStep ? kPushStep : ((chunk + kPushStep - 1) / kPushStep) * kPushStep;
     for (long long e0l = (long long)gwarp * chunk; e0l < E; e0l += (long long)nwarps * chunk) {
@@ -255,73 +262,53 @@ __device__ __forceinline__ void ms_push_scatter(const MsArgs& a, int cur, uint32
 #pragma unroll
             for (int t = 0; t < kPushIlp; ++t) {
                 const int32_t u = ps.u[t], v = ps.v[t];
-                bool touched = false;
+                bool first = false;
                 if (u >= 0 && !((a.D[v >> 5] >> (v & 31)) & 1u)) {
+                    bool any = false;
                     for (int32_t c = 0; c < a.W; c += CW) {
 #pragma unroll
                         for (int j = 0; j < CW; ++j) {
-                            const unsigned long long f = a.F[(size_t)u * a.W + c + j];
-                            if (f) {
-                                atomicOr(a.N + (size_t)v * a.W + c + j, f);
-                                touched = true;
+                            const size_t iu = (size_t)u * a.W + c + j, iv = (size_t)v * a.W + c + j;
+                            const unsigned long long cand = Fc[iu] & ~a.V[iv];
+                            if (!cand) continue;
+                            const unsigned long long old = atomicOr(a.V + iv, cand);
+                            const unsigned long long gained = cand & ~old;
+                            if (!gained) continue;
+                            const unsigned long long fold = atomicOr(Fn + iv, gained);
+                            if (a.W == 1) {
+                                first |= fold == 0ull;
+                                if (((old | cand) & full0) == full0) atomicOr(a.D + (v >> 5), 1u << (v & 31));
+                            }
+                            any = true;
+                            acc.n_new += (unsigned long long)__popcll(gained);
+                            unsigned long long m = gained;
+                            while (m) {
+                                const int b = __ffsll((long long)m) - 1;
+                                m &= m - 1;
+                                store_depth(a, (c + j) * 64 + b, v, L + 1);
                             }
                         }
                     }
+                    if (a.W > 1 && any) first = !(atomicOr(Tn + (v >> 5), 1u << (v & 31)) & (1u << (v & 31)));
                 }
-                bool first = false;
-                if (touched) first = !(atomicOr(a.T + (v >> 5), 1u << (v & 31)) & (1u << (v & 31)));
-                // warp-aggregated append to the touched list
-                const uint32_t m = __ballot_sync(0xffffffffu, first);
-                if (m) {
-                    unsigned long long base_pos = 0;
-                    if (lane == 0) base_pos = atomicAdd(&cout->list, (unsigned long long)__popc(m));
-                    base_pos = __shfl_sync(0xffffffffu, base_pos, 0);
-                    if (first) a.tlist[base_pos + __popc(m & lanemask_lt())] = v;
-                }
+                st.put(first, v);
             }
         }
-    }
-}
-
-// new = N & ~V for the touched vertices; V |= new, F = new, N = 0, depth.
-template <int CW>
-__device__ __forceinline__ void ms_push_finalize(const MsArgs& a, int32_t L, uint32_t count, Stage& st, Acc& acc) {
-    const long long gtid = (long long)blockIdx.x * kMsThreads + threadIdx.x;
-    const long long gstride = (long long)gridDim.x * kMsThreads;
-    const long long rounds = ((long long)count + gstride - 1) / gstride;
-    for (long long r = 0; r < rounds; ++r) {  // warp-uniform trip count: st.put needs all lanes
-        const long long k = r * gstride + gtid;
-        const bool mine = k < count;
-        const int32_t v = mine ? a.tlist[k] : 0;
-        bool any_new = false, full = true;
-        for (int32_t w = 0; w < a.W; ++w) {
-            unsigned long long nw = 0;
-            if (mine) {
-                const size_t idx = (size_t)v * a.W + w;
-                const unsigned long long nn = a.N[idx];
-                const unsigned long long vv = a.V[idx];
-                nw = nn & ~vv & lane_mask(a.S, w);
-                a.V[idx] = vv | nw;
-                a.F[idx] = nw;
-                a.N[idx] = 0ull;
-                full &= ((vv | nw) & lane_mask(a.S, w)) == lane_mask(a.S, w);
-                acc.n_new += (unsigned long long)__popcll(nw);
-                any_new |= nw != 0ull;
-            }
-            unsigned long long m = nw;
-            while (m) {
-                const int b = __ffsll((long long)m) - 1;
-                m &= m - 1;
-                store_depth(a, w * 64 + b, v, L + 1);
-            }
-        }
-        if (mine) {
-            atomicAnd(a.T + (v >> 5), ~(1u << (v & 31)));
-            if (full) atomicOr(a.D + (v >> 5), 1u << (v & 31));
-        }
-        st.put(mine && any_new, v);
     }
     st.flush();
+}
+
+// Clear F_{(L+2) mod 3} and T_{(L+2) mod 3} for the active list of level L - 1:
+// those buffers were last read at level L - 1 and are written again at level L + 1.
+__device__ __forceinline__ void ms_clear_prev(const MsArgs& a, const int32_t* ids, uint32_t count,
+                                              unsigned long long* F, uint32_t* T) {
+    const long long gtid = (long long)blockIdx.x * kMsThreads + threadIdx.x;
+    const long long gstride = (long long)gridDim.x * kMsThreads;
+    for (long long k = gtid; k < count; k += gstride) {
+        const int32_t v = ids[k];
+        for (int32_t w = 0; w < a.W; ++w) F[(size_t)v * a.W + w] = 0ull;
+        T[v >> 5] = 0u;  // every bit of T_{(L+2) mod 3} belongs to that list: racing writers all store zero
+    }
 }
 
 // ---------------------------------------------------------------- kernel
@@ -338,15 +325,19 @@ __global__ void __launch_bounds__(kMsThreads, 1) ms_bfs_kernel(MsArgs a) {
     unsigned int* barc = a.bar->count + a.bar_parity;
     unsigned int bar_round = 0;
     unsigned long long t_mark = gtid == 0 ? global_timer_ns() : 0ull;
-    // ---- init: V = N = 0, D = T = 0, depth = -1
+    // ---- init: V = F_k = 0, D = T_k = 0, depth = -1
     const size_t nw_total = (size_t)a.n * (size_t)a.W;
     for (size_t i = gtid; i < nw_total; i += gstride) {
         a.V[i] = 0ull;
-        a.N[i] = 0ull;
+        a.Fb[0][i] = 0ull;
+        a.Fb[1][i] = 0ull;
+        a.Fb[2][i] = 0ull;
     }
     for (long long w = gtid; w < a.nwords; w += gstride) {
         a.D[w] = 0u;
-        a.T[w] = 0u;
+        a.Tb[0][w] = 0u;
+        a.Tb[1][w] = 0u;
+        a.Tb[2][w] = 0u;
     }
     const size_t nd = (size_t)a.S * (size_t)a.n;
     if (a.rows) {
@@ -384,7 +375,7 @@ __global__ void __launch_bounds__(kMsThreads, 1) ms_bfs_kernel(MsArgs a) {
     // F = V for the (distinct) source vertices; they form the first active list
     {
         Acc acc0;
-        Stage st{stage_mem + wib, 0, a.ctr + 0, a.q[0], a.qp[0], a.qd[0], a.out_ptr, a.in_ptr, 1, 0, &acc0};
+        Stage st{stage_mem + wib, 0, a.ctr + 0, a.ids[0], a.qp[0], a.qd[0], a.out_ptr, a.in_ptr, 1, 0, &acc0};
         const long long rounds = ((long long)a.S + gstride - 1) / gstride;
         for (long long r = 0; r < rounds; ++r) {
             const long long b = r * gstride + gtid;
@@ -392,9 +383,9 @@ __global__ void __launch_bounds__(kMsThreads, 1) ms_bfs_kernel(MsArgs a) {
             int32_t s = 0;
             if (b < a.S) {
                 s = a.src[b];
-                take = !(atomicOr(a.T + (s >> 5), 1u << (s & 31)) & (1u << (s & 31)));
+                take = !(atomicOr(a.Tb[0] + (s >> 5), 1u << (s & 31)) & (1u << (s & 31)));
                 if (take)
-                    for (int32_t w = 0; w < a.W; ++w) a.F[(size_t)s * a.W + w] = a.V[(size_t)s * a.W + w];
+                    for (int32_t w = 0; w < a.W; ++w) a.Fb[0][(size_t)s * a.W + w] = a.V[(size_t)s * a.W + w];
             }
             st.put(take, s);
         }
@@ -405,14 +396,15 @@ __global__ void __launch_bounds__(kMsThreads, 1) ms_bfs_kernel(MsArgs a) {
     if (!grid_barrier(barc, gridDim.x, bar_round, a.status, a.timeout_ns)) return;
     for (long long b = gtid; b < a.S; b += gstride) {
         const int32_t s = a.src[b];
-        a.T[s >> 5] = 0u;  // racing writers all store zero
+        a.Tb[0][s >> 5] = 0u;  // racing writers all store zero
     }
     if (threadIdx.x == 0) lvl[4] = ld_volatile_u64(&a.ctr[0].q);
     if (!grid_barrier(barc, gridDim.x, bar_round, a.status, a.timeout_ns)) return;
     unsigned long long qv = lvl[4];
-    int cur = 0;
+    uint32_t prev_count = 0;  // size of the active list of level L - 1
     long long pairs = a.S;
     for (int32_t L = 0;; ++L) {
+        const int r0 = L % 3, r1 = (L + 1) % 3, r2 = (L + 2) % 3, p0 = L & 1, p1 = p0 ^ 1;
         LevelCtr* cout = a.ctr + ((L + 1) % 3);
         if (gtid == 0) {
             LevelCtr z = {};
@@ -427,16 +419,12 @@ __global__ void __launch_bounds__(kMsThreads, 1) ms_bfs_kernel(MsArgs a) {
             return;
         }
         Acc acc;
-        Stage st{stage_mem + wib, 0, cout, a.q[cur ^ 1], a.qp[cur ^ 1], a.qd[cur ^ 1], a.out_ptr, a.in_ptr, 1, 0, &acc};
-        if (dir == GBX_DIR_PUSH) {
-            ms_push_scatter<CW>(a, cur, qcount, qedges, cout);
-            if (!grid_barrier(barc, gridDim.x, bar_round, a.status, a.timeout_ns)) return;
-            if (threadIdx.x == 0) lvl[5] = ld_volatile_u64(&cout->list);
-            __syncthreads();
-            ms_push_finalize<CW>(a, L, (uint32_t)lvl[5], st, acc);
-        } else {
-            ms_pull<CW>(a, L, st, acc);
-        }
+        Stage st{stage_mem + wib, 0, cout, a.ids[r1], a.qp[p1], a.qd[p1], a.out_ptr, a.in_ptr, 1, 0, &acc};
+        ms_clear_prev(a, a.ids[r2], prev_count, a.Fb[r2], a.Tb[r2]);
+        if (dir == GBX_DIR_PUSH)
+            ms_push<CW>(a, L, a.ids[r0], a.qp[p0], a.qd[p0], qcount, qedges, a.Fb[r0], a.Fb[r1], a.Tb[r1], st, acc);
+        else
+            ms_pull<CW>(a, L, a.Fb[r1], st, acc);
         {
             const unsigned long long x = warp_sum_u64(acc.n_new);
             const unsigned long long y = warp_sum_u64(acc.mf);
@@ -453,14 +441,13 @@ __global__ void __launch_bounds__(kMsThreads, 1) ms_bfs_kernel(MsArgs a) {
             lvl[1] = ld_volatile_u64(&cout->mf_new);
             lvl[3] = ld_volatile_u64(&cout->e_exam);
             lvl[4] = ld_volatile_u64(&cout->q);
-            lvl[5] = ld_volatile_u64(&cout->list);
         }
         __syncthreads();
         qv = lvl[4];
         if (dir == GBX_DIR_PULL) {
             // V |= F for the vertices the pull found (their new lanes were kept apart so the
             // level read V as it was before it started)
-            ms_pull_commit<CW>(a, a.q[cur ^ 1], (uint32_t)qv);
+            ms_pull_commit<CW>(a, a.ids[r1], (uint32_t)qv, a.Fb[r1]);
             if (!grid_barrier(barc, gridDim.x, bar_round, a.status, a.timeout_ns)) return;
         }
         const long long n_new = (long long)lvl[0];
@@ -488,7 +475,7 @@ __global__ void __launch_bounds__(kMsThreads, 1) ms_bfs_kernel(MsArgs a) {
             return;
         }
         pairs = n_new;
-        cur ^= 1;
+        prev_count = qcount;
     }
 }
 
@@ -500,14 +487,15 @@ gbx_status ms_reserve(Workspace& w, int32_t n, int32_t S, cudaStream_t s) {
         if (w.msV) {
             GBX_CUDA_TRY(cudaStreamSynchronize(s));
             cudaFree(w.msV);
-            cudaFree(w.msF);
-            cudaFree(w.msN);
-            w.msV = w.msF = w.msN = nullptr;
+            w.msV = nullptr;
+            for (auto& p : w.msF) {
+                cudaFree(p);
+                p = nullptr;
+            }
             w.ms_cap_words = 0;
         }
         GBX_CUDA_TRY(cudaMalloc((void**)&w.msV, sizeof(unsigned long long) * (size_t)need));
-        GBX_CUDA_TRY(cudaMalloc((void**)&w.msF, sizeof(unsigned long long) * (size_t)need));
-        GBX_CUDA_TRY(cudaMalloc((void**)&w.msN, sizeof(unsigned long long) * (size_t)need));
+        for (auto& p : w.msF) GBX_CUDA_TRY(cudaMalloc((void**)&p, sizeof(unsigned long long) * (size_t)need));
         w.ms_cap_words = need;
     }
     return GBX_OK;
@@ -516,7 +504,7 @@ gbx_status ms_reserve(Workspace& w, int32_t n, int32_t S, cudaStream_t s) {
 int64_t ms_scratch_bytes(int32_t n, int32_t S) {
     const int32_t w_raw = (S + 63) / 64;
     const int cw = w_raw >= 4 ? 4 : (w_raw >= 2 ? 2 : 1);
-    return 3ll * 8ll * (int64_t)n * ((w_raw + cw - 1) / cw * cw);
+    return 4ll * 8ll * (int64_t)n * ((w_raw + cw - 1) / cw * cw);
 }
 
 template <int CW>
@@ -555,17 +543,19 @@ gbx_status ms_run(Graph* G, Workspace& w, int32_t S, const int32_t* src_dev, voi
     a.in_col = G->in_col;
     a.nz_in = G->nz_in;
     a.V = w.msV;
-    a.F = w.msF;
-    a.N = w.msN;
+    for (int k = 0; k < 3; ++k) a.Fb[k] = w.msF[k];
     a.D = w.bm[2];
-    a.T = w.bm[3];
-    a.tlist = w.list;
+    a.Tb[0] = w.bm[3];
+    a.Tb[1] = w.bm[0];
+    a.Tb[2] = w.bm[1];
     a.depth = depth;
     a.rows = rows;
     a.depth16 = depth16;
     a.src = src_dev;
+    a.ids[0] = w.q[0];
+    a.ids[1] = w.q[1];
+    a.ids[2] = w.list;
     for (int i = 0; i < 2; ++i) {
-        a.q[i] = w.q[i];
         a.qp[i] = w.qp[i];
         a.qd[i] = w.qd[i];
     }
