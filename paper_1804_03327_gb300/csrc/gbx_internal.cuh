@@ -100,6 +100,8 @@ struct Workspace {
     // batched multi-source BFS scratch (allocated on first use, grown as needed)
     unsigned long long* msV = nullptr;                     // visited lanes [n][W]
     unsigned long long* msF[3] = {nullptr, nullptr, nullptr};  // lanes found per level, rotating [n][W]
+    int32_t* msT = nullptr;                                    // vertices a wide push level touched [n]
+    int64_t ms_t_cap = 0;                                      // entries msT holds
     int64_t ms_cap_words = 0;
     int32_t* ms_src = nullptr;  // device copy of the sources
     int32_t* ms_src_pinned = nullptr;

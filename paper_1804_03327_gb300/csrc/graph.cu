@@ -159,6 +159,7 @@ void workspace_release(Workspace& w) {
     f(w.flag);
     f(w.msV);
     for (auto& p : w.msF) f(p);
+    f(w.msT);
     f(w.ms_src);
     if (w.ms_src_pinned) cudaFreeHost(w.ms_src_pinned);
     if (w.ms_src_ready) cudaEventDestroy(w.ms_src_ready);

@@ -12,10 +12,14 @@
 //   D         one bit per vertex: every lane visited (pull skips it without loads);
 //   T_k       one bit per vertex: listed for level L + 1 (W > 1), rotating like F.
 // Each level runs in the direction chosen for the whole batch:
-//   push (Eq 5 lane-wise): the active list's edges are split evenly over warps;
-//     each edge claims the lanes F[u] & ~V[v] with a 64-bit atomicOr on V[v];
-//     the lanes it gained are new (unique claimant): their depth is written, they
-//     are ORed into F_next[v], and the first claimant of v lists it.
+//   push (Eq 5 lane-wise): the active list's edges are split evenly over warps.
+//     One word per vertex (S <= 64): each edge claims the lanes F[u] & ~V[v] with a
+//     64-bit atomicOr on V[v]; the lanes it gained are new (unique claimant): their
+//     depth is written, they are ORed into F_next[v], and the first claimant of v
+//     lists it -- one phase.  Wider batches: each edge ORs F[u] & ~V[v] into
+//     F_next[v] with reductions and lists v once; after a grid barrier a finalising
+//     pass over the touched vertices keeps new = F_next & ~V, sets V |= new and
+//     writes the depths (one returning atomic per word and edge would cost more).
 //   pull (Eq 4 lane-wise, masking + early exit + operand reuse): every vertex with
 //     an unvisited lane ORs V of its in-neighbours (V is the state before this
 //     level) and stops as soon as every unvisited lane is covered; new = acc & ~V.
@@ -41,6 +45,7 @@ struct MsArgs {
     unsigned long long* Fb[3];  // rotating found-lane buffers
     uint32_t* D;                // all lanes visited
     uint32_t* Tb[3];            // rotating "listed" bitmaps
+    int32_t* tlist;             // vertices touched by a wide push level
     void* depth;        // [S][n], used when rows is NULL
     void* const* rows;  // optional: lane b writes its n depths to rows[b]
     int depth16;
@@ -263,7 +268,22 @@ __device__ __forceinline__ void ms_push(const MsArgs& a, int32_t L, const int32_
             for (int t = 0; t < kPushIlp; ++t) {
                 const int32_t u = ps.u[t], v = ps.v[t];
                 bool first = false;
-                if (u >= 0 && !((a.D[v >> 5] >> (v & 31)) & 1u)) {
+                if (CW > 1 && u >= 0 && !((a.D[v >> 5] >> (v & 31)) & 1u)) {
+                    // wide batch: accumulate, finalised after the barrier
+                    bool touched = false;
+                    for (int32_t c = 0; c < a.W; c += CW) {
+#pragma unroll
+                        for (int j = 0; j < CW; ++j) {
+                            const size_t iu = (size_t)u * a.W + c + j, iv = (size_t)v * a.W + c + j;
+                            const unsigned long long cand = Fc[iu] & ~a.V[iv];
+                            if (cand) {
+                                atomicOr(Fn + iv, cand);  // result unused: a reduction
+                                touched = true;
+                            }
+                        }
+                    }
+                    if (touched) first = !(atomicOr(Tn + (v >> 5), 1u << (v & 31)) & (1u << (v & 31)));
+                } else if (CW == 1 && u >= 0 && !((a.D[v >> 5] >> (v & 31)) & 1u)) {
                     bool any = false;
                     for (int32_t c = 0; c < a.W; c += CW) {
 #pragma unroll
@@ -274,10 +294,11 @@ __device__ __forceinline__ void ms_push(const MsArgs& a, int32_t L, const int32_
                             const unsigned long long old = atomicOr(a.V + iv, cand);
                             const unsigned long long gained = cand & ~old;
                             if (!gained) continue;
-                            const unsigned long long fold = atomicOr(Fn + iv, gained);
                             if (a.W == 1) {
-                                first |= fold == 0ull;
+                                first |= atomicOr(Fn + iv, gained) == 0ull;
                                 if (((old | cand) & full0) == full0) atomicOr(a.D + (v >> 5), 1u << (v & 31));
+                            } else {
+                                atomicOr(Fn + iv, gained);  // result unused: a reduction; T_next lists v
                             }
                             any = true;
                             acc.n_new += (unsigned long long)__popcll(gained);
@@ -289,11 +310,63 @@ __device__ __forceinline__ void ms_push(const MsArgs& a, int32_t L, const int32_
                             }
                         }
                     }
-                    if (a.W > 1 && any) first = !(atomicOr(Tn + (v >> 5), 1u << (v & 31)) & (1u << (v & 31)));
+                    (void)any;
                 }
-                st.put(first, v);
+                if (CW == 1) {
+                    st.put(first, v);
+                } else {
+                    // warp-aggregated append to the touched list
+                    const int lane = threadIdx.x & 31;
+                    const uint32_t m = __ballot_sync(0xffffffffu, first);
+                    if (m) {
+                        unsigned long long base_pos = 0;
+                        if (lane == 0) base_pos = atomicAdd(&st.cout->list, (unsigned long long)__popc(m));
+                        base_pos = __shfl_sync(0xffffffffu, base_pos, 0);
+                        if (first) a.tlist[base_pos + __popc(m & lanemask_lt())] = v;
+                    }
+                }
             }
         }
+    }
+    if (CW == 1) st.flush();
+}
+
+// Wide push levels, after the barrier: new = F_next & ~V for the touched vertices;
+// V |= new, F_next = new, depth, "all lanes" map; the touched ones with new lanes
+// form the next active list.  Every T_next bit belongs to a touched vertex, so the
+// words are cleared whole (racing writers all store zero).
+template <int CW>
+__device__ __forceinline__ void ms_push_finalize(const MsArgs& a, int32_t L, uint32_t count, unsigned long long* Fn,
+                                                 uint32_t* Tn, Stage& st, Acc& acc) {
+    const long long gtid = (long long)blockIdx.x * kMsThreads + threadIdx.x;
+    const long long gstride = (long long)gridDim.x * kMsThreads;
+    const long long rounds = ((long long)count + gstride - 1) / gstride;
+    for (long long r = 0; r < rounds; ++r) {  // warp-uniform trip count: st.put needs all lanes
+        const long long k = r * gstride + gtid;
+        const bool mine = k < count;
+        const int32_t v = mine ? a.tlist[k] : 0;
+        bool any_new = false, full = true;
+        if (mine) {
+            for (int32_t w = 0; w < a.W; ++w) {
+                const size_t idx = (size_t)v * a.W + w;
+                const unsigned long long vv = a.V[idx];
+                const unsigned long long nw = Fn[idx] & ~vv & lane_mask(a.S, w);
+                a.V[idx] = vv | nw;
+                Fn[idx] = nw;
+                full &= ((vv | nw) & lane_mask(a.S, w)) == lane_mask(a.S, w);
+                acc.n_new += (unsigned long long)__popcll(nw);
+                any_new |= nw != 0ull;
+                unsigned long long m = nw;
+                while (m) {
+                    const int b = __ffsll((long long)m) - 1;
+                    m &= m - 1;
+                    store_depth(a, w * 64 + b, v, L + 1);
+                }
+            }
+            Tn[v >> 5] = 0u;
+            if (full) atomicOr(a.D + (v >> 5), 1u << (v & 31));
+        }
+        st.put(mine && any_new, v);
     }
     st.flush();
 }
@@ -421,10 +494,17 @@ __global__ void __launch_bounds__(kMsThreads, 1) ms_bfs_kernel(MsArgs a) {
         Acc acc;
         Stage st{stage_mem + wib, 0, cout, a.ids[r1], a.qp[p1], a.qd[p1], a.out_ptr, a.in_ptr, 1, 0, &acc};
         ms_clear_prev(a, a.ids[r2], prev_count, a.Fb[r2], a.Tb[r2]);
-        if (dir == GBX_DIR_PUSH)
+        if (dir == GBX_DIR_PUSH) {
             ms_push<CW>(a, L, a.ids[r0], a.qp[p0], a.qd[p0], qcount, qedges, a.Fb[r0], a.Fb[r1], a.Tb[r1], st, acc);
-        else
+            if (CW > 1) {
+                if (!grid_barrier(barc, gridDim.x, bar_round, a.status, a.timeout_ns)) return;
+                if (threadIdx.x == 0) lvl[5] = ld_volatile_u64(&cout->list);
+                __syncthreads();
+                ms_push_finalize<CW>(a, L, (uint32_t)lvl[5], a.Fb[r1], a.Tb[r1], st, acc);
+            }
+        } else {
             ms_pull<CW>(a, L, a.Fb[r1], st, acc);
+        }
         {
             const unsigned long long x = warp_sum_u64(acc.n_new);
             const unsigned long long y = warp_sum_u64(acc.mf);
@@ -498,13 +578,23 @@ gbx_status ms_reserve(Workspace& w, int32_t n, int32_t S, cudaStream_t s) {
         for (auto& p : w.msF) GBX_CUDA_TRY(cudaMalloc((void**)&p, sizeof(unsigned long long) * (size_t)need));
         w.ms_cap_words = need;
     }
+    if (w.ms_t_cap < (int64_t)n + 1) {
+        if (w.msT) {
+            GBX_CUDA_TRY(cudaStreamSynchronize(s));
+            cudaFree(w.msT);
+            w.msT = nullptr;
+            w.ms_t_cap = 0;
+        }
+        GBX_CUDA_TRY(cudaMalloc((void**)&w.msT, sizeof(int32_t) * ((size_t)n + 1)));
+        w.ms_t_cap = (int64_t)n + 1;
+    }
     return GBX_OK;
 }
 
 int64_t ms_scratch_bytes(int32_t n, int32_t S) {
     const int32_t w_raw = (S + 63) / 64;
     const int cw = w_raw >= 4 ? 4 : (w_raw >= 2 ? 2 : 1);
-    return 4ll * 8ll * (int64_t)n * ((w_raw + cw - 1) / cw * cw);
+    return 4ll * 8ll * (int64_t)n * ((w_raw + cw - 1) / cw * cw) + 4ll * ((int64_t)n + 1);
 }
 
 template <int CW>
@@ -529,7 +619,7 @@ gbx_status ms_run(Graph* G, Workspace& w, int32_t S, const int32_t* src_dev, voi
     const int32_t w_raw = (S + 63) / 64;
     const int cw = w_raw >= 4 ? 4 : (w_raw >= 2 ? 2 : 1);
     const int32_t W = (w_raw + cw - 1) / cw * cw;
-    GBX_CHECK(w.ms_cap_words >= (int64_t)G->n * W && w.n_cap >= G->n, GBX_ERR_INVALID_VALUE,
+    GBX_CHECK(w.ms_cap_words >= (int64_t)G->n * W && w.n_cap >= G->n && w.ms_t_cap > G->n, GBX_ERR_INVALID_VALUE,
               "batch scratch not reserved");
     MsArgs a;
     a.n = G->n;
@@ -548,6 +638,7 @@ gbx_status ms_run(Graph* G, Workspace& w, int32_t S, const int32_t* src_dev, voi
     a.Tb[0] = w.bm[3];
     a.Tb[1] = w.bm[0];
     a.Tb[2] = w.bm[1];
+    a.tlist = w.msT;
     a.depth = depth;
     a.rows = rows;
     a.depth16 = depth16;
