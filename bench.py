@@ -214,12 +214,45 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+_OG_CACHE = {}
+
+
+def oracle_graph(n, src, dst):
+    """The oracle's CSR of an edge list, built once per (src, dst) arrays per run."""
+    import oracle
+
+    key = (id(src), id(dst), n)
+    if key not in _OG_CACHE:
+        _OG_CACHE[key] = (oracle.graph(n, src, dst), src, dst)  # the arrays are kept alive with the key
+    return _OG_CACHE[key][0]
+
+
+def cpu_parallel_oracle(jobs, cores=None):
+    """The oracle's single-source queue BFS, one source per host thread on all of
+    the host's cores (ctypes releases the GIL during each C call): the CPU
+    baseline of the batched and served forms.  jobs = [(oracle graph, sources,
+    reached undirected edges per source)]; returns GTEPS over the whole sample."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+
+    cores = cores or os.cpu_count() or 1
+    tasks = [(og, int(x)) for og, srcs, _ in jobs for x in srcs]
+    edges = sum(int(sum(r)) for _, _, r in jobs)
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(cores) as ex:
+        list(ex.map(lambda t: oracle.bfs(t[0], t[1]), tasks))
+    dt = time.perf_counter() - t0
+    return {"value": edges / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{len(tasks)} single-source BFS, one per thread ({dt:.1f} s)"}
+
+
 def cpu_oracle_baseline(n, src, dst, sources, sample: int):
     """The CPU oracle (single-threaded C queue BFS) on the first `sample`
     sources of the same workload; returns (GTEPS, seconds, edges)."""
     import oracle
 
-    og = oracle.graph(n, src, dst)
+    og = oracle_graph(n, src, dst)
     deg = np.diff(og.out_ptr)
     edges = 0
     t0 = time.perf_counter()
@@ -559,8 +592,11 @@ def batched_measurements(g, n, sources, reached, single_value, args):
     import synth as _synth
     t = time_batch(g, sources, n, tune_srcs=_synth.sources(n, *args._edges, len(sources), seed=SEED + 200))
     v = sum(reached) / t / 1e9
+    import oracle
+    og_main = oracle_graph(n, *args._edges)
     res["same_sources_as_one_batch"] = {"workload": WORKLOAD, "S": len(sources), "ms": t * 1e3, "value": v,
-                                        "unit": UNIT, "vs_single_source": v / single_value}
+                                        "unit": UNIT, "vs_single_source": v / single_value,
+                                        "cpu_baseline": cpu_parallel_oracle([(og_main, sources, reached)])}
     cfg4 = []
     for name, gen in [("rmat21-ef16", lambda: synth.rmat_edges(21, EDGE_FACTOR, seed=SEED)),
                       ("grid2048-del1pct", lambda: synth.grid_edges(2048, 2048, 0.01, seed=SEED))]:
@@ -580,12 +616,14 @@ def batched_measurements(g, n, sources, reached, single_value, args):
         torch.cuda.synchronize()
         single_s = e0.elapsed_time(e1) / 1e3 / 64
         reach = reached_of(gg, all_src, nn)
+        import oracle
+        cpu_b = cpu_parallel_oracle([(oracle_graph(nn, ss, dd), all_src[:64], reach[:64])])
         for S in widths:
             tb = time_batch(gg, all_src[:S], nn, reps=1 if name.startswith("grid") else 3, tune_srcs=tune_all[:S])
             edges = sum(reach[:S])
             cfg4.append({"graph": name, "S": S, "ms": tb * 1e3, "value": edges / tb / 1e9, "unit": UNIT,
                          "single_source_value": edges / (single_s * S) / 1e9,
-                         "speedup_vs_single_source": single_s * S / tb})
+                         "speedup_vs_single_source": single_s * S / tb, "cpu_baseline": cpu_b})
         gg.free()
     res["configs"] = cfg4
     return res
@@ -628,7 +666,8 @@ def served_measurement(main_graph, args):
             for s1 in cand:
                 if dn[int(s1)] >= 0:
                     reach[int(s1)] = e
-        graphs.append({"name": name, "g": g, "n": n, "cand": cand, "reach": reach, "own": gen is not None})
+        graphs.append({"name": name, "g": g, "n": n, "cand": cand, "reach": reach, "own": gen is not None,
+                       "edges": (src, dst)})
     slots = 8
     srv = gbx.Server(max_batch=64, slots=slots, depth_type=gbx.DEPTH_I16, max_pending=1 << 16)
     rows = 2048
@@ -689,7 +728,15 @@ def served_measurement(main_graph, args):
         if gi["own"]:
             gi["g"].free()
     mean_edges = float(np.mean([np.mean(list(gi["reach"].values())) for gi in graphs]))
+    # CPU baseline: the same mix answered by the oracle on all host cores (8 queries per graph)
+    import oracle
+    jobs = []
+    for gi in graphs:
+        qs = [int(x) for x in gi["cand"][:8]]
+        jobs.append((oracle_graph(gi["n"], *gi["edges"]), qs, [gi["reach"][x] for x in qs]))
+    cpu_s = cpu_parallel_oracle(jobs)
     return {"graphs": [gi["name"] for gi in graphs], "at_configured_rate": saturated,
+            "cpu_baseline": cpu_s,
             "at_half_saturated_throughput": sustainable,
             "mean_reached_edges_per_query": mean_edges,
             "gteps_needed_for_configured_rate": args.serve_rate * mean_edges / 1e9,

@@ -144,13 +144,26 @@ extern "C" gbx_status gbx_autotune(gbx_graph* g, int32_t kind, const int32_t* so
     }
     gbx_desc winner = base;
     double win_ms = 1e300;
+    std::vector<double> cand_ms(cand.size(), 1e300);
     for (size_t c = 0; c < cand.size() && st == GBX_OK; ++c) {
         double ms = 0.0;
         st = time_desc(cand[c], &ms);
+        cand_ms[c] = ms;
         if (st == GBX_OK && ms < win_ms) {
             win_ms = ms;
             winner = cand[c];
         }
+    }
+    // Batches: the time is a step function of alpha (a level either pushes or pulls),
+    // and other sources put the step elsewhere; among thresholds within 3 % of the
+    // best, the largest (pulling latest) is the safest choice.
+    if (kind == GBX_TUNE_BATCH && st == GBX_OK) {
+        const double best = win_ms;
+        for (size_t c = 0; c < cand.size(); ++c)
+            if (cand_ms[c] <= best * 1.03 && cand[c].alpha > winner.alpha) {
+                winner = cand[c];
+                win_ms = cand_ms[c];
+            }
     }
     // second stage: lane probe depth and persistent blocks per SM on the winning rule
     const int32_t probes_bfs[] = {8, 32};
