@@ -57,6 +57,7 @@ def parse():
     p.add_argument("--no-served", action="store_true", help="skip the serving measurement")
     p.add_argument("--serve-seconds", type=float, default=2.0)
     p.add_argument("--serve-rate", type=float, default=20000.0)
+    p.add_argument("--serve-slots", type=int, default=4, help="server slots (concurrent batches; 4 measured best of 1-16)")
     p.add_argument("--sweep", action="store_true",
                    help="masked-mxv operator sweep (RMAT scale 20 and the 2048x2048 grid) instead of the BFS line")
     p.add_argument("--ablation", action="store_true",
@@ -668,7 +669,7 @@ def served_measurement(main_graph, args):
                     reach[int(s1)] = e
         graphs.append({"name": name, "g": g, "n": n, "cand": cand, "reach": reach, "own": gen is not None,
                        "edges": (src, dst)})
-    slots = 8
+    slots = args.serve_slots
     srv = gbx.Server(max_batch=64, slots=slots, depth_type=gbx.DEPTH_I16, max_pending=1 << 16)
     rows = 2048
     for gi in graphs:
