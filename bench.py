@@ -675,6 +675,12 @@ def served_measurement(main_graph, args):
     for gi in graphs:
         gi["id"] = srv.add_graph(gi["g"])
         gi["pool"] = torch.empty((rows, gi["n"]), dtype=torch.int16, device="cuda")
+        # per-graph batch descriptor, autotuned on 64 other seeded sources of that graph
+        src_e, dst_e = gi["edges"]
+        tune = synth.sources(gi["n"], src_e, dst_e, 64, seed=SEED + 400)
+        bdesc, _ = gbx.autotune(gi["g"], gbx.TUNE_BATCH, tune)
+        srv.set_graph_desc(gi["id"], bdesc)
+        gi["alpha"] = float(bdesc.alpha)
 
     def run(rate, seed):
         for gi in graphs:
@@ -741,7 +747,8 @@ def served_measurement(main_graph, args):
             "at_half_saturated_throughput": sustainable,
             "mean_reached_edges_per_query": mean_edges,
             "gteps_needed_for_configured_rate": args.serve_rate * mean_edges / 1e9,
-            "server": {"slots": slots, "max_batch": 64, "depth": "int16", "scratch_bytes": st["scratch_bytes"]},
+            "server": {"slots": slots, "max_batch": 64, "depth": "int16", "scratch_bytes": st["scratch_bytes"],
+                       "batch_alpha_per_graph": {gi["name"]: gi["alpha"] for gi in graphs}},
             "note": "latency = scheduled arrival -> completion seen by the client's poll; rates and GTEPS over "
                     "queries arriving after a 0.5 s warm-up; graph uniform per query, source uniform over 256 "
                     "seeded candidates per graph"}

@@ -443,6 +443,12 @@ gbx_status gbx_server_create(gbx_server** out, const gbx_server_config* cfg);
 gbx_status gbx_server_add_graph(gbx_server* s, gbx_graph* g, int32_t* graph_id);
 /* Lane width (sources per batch) the server chose for a graph. */
 gbx_status gbx_server_graph_lanes(gbx_server* s, int32_t graph_id, int32_t* lanes);
+/* Descriptor of the batches of one graph (direction, alpha, pull_probe as in
+ * gbx_bfs_batch; e.g. from gbx_autotune with GBX_TUNE_BATCH on sources of that
+ * graph).  Default: gbx_desc_init with alpha = the config's alpha.  Applies to
+ * batches launched after the call.  Errors: NULL_POINTER, INVALID_INDEX (graph
+ * id), INVALID_VALUE (desc fields), NOT_SUPPORTED (push_sort). */
+gbx_status gbx_server_set_graph_desc(gbx_server* s, int32_t graph_id, const gbx_desc* desc);
 /* Queue a BFS from `source` on graph `graph_id`; its depths (n entries of the
  * server's depth type, device memory, caller-owned, untouched until the query
  * completes) go to depth_out.  May start batches.  Errors: BUSY (queue full),

@@ -48,6 +48,7 @@ struct Slot {
 struct GraphEntry {
     Graph* g = nullptr;
     int32_t lanes = 0;
+    gbx_desc desc;  // descriptor of this graph's batches (direction threshold, lane probe)
     std::deque<Query> pending;
 };
 
@@ -144,9 +145,7 @@ static gbx_status dispatch(Server* S) {
         S->queued -= nb;
         GBX_CUDA_TRY(cudaMemcpyAsync(sl.src_dev, sl.src_pinned, sizeof(int32_t) * nb, cudaMemcpyHostToDevice, sl.stream));
         GBX_CUDA_TRY(cudaMemcpyAsync(sl.rows_dev, sl.rows_pinned, sizeof(void*) * nb, cudaMemcpyHostToDevice, sl.stream));
-        gbx_desc d;
-        gbx_desc_init(&d);
-        d.alpha = S->cfg.alpha;
+        const gbx_desc d = ge.desc;
         sl.t_launch = S->now();
         GBX_TRY(ms_run(ge.g, sl.ws, nb, sl.src_dev, nullptr, sl.rows_dev, S->cfg.depth_type == GBX_DEPTH_I16 ? 1 : 0,
                        d, (int)S->slots.size(), sl.stream));
@@ -248,6 +247,8 @@ extern "C" gbx_status gbx_server_add_graph(gbx_server* srv, gbx_graph* g, int32_
     GraphEntry ge;
     ge.g = G;
     ge.lanes = lanes;
+    gbx_desc_init(&ge.desc);
+    ge.desc.alpha = S->cfg.alpha;
     S->graphs.push_back(ge);
     *graph_id = (int32_t)S->graphs.size() - 1;
     return GBX_OK;
@@ -260,6 +261,24 @@ extern "C" gbx_status gbx_server_graph_lanes(gbx_server* srv, int32_t graph_id, 
     std::lock_guard<std::mutex> lock(S->mu);
     GBX_CHECK(graph_id >= 0 && graph_id < (int32_t)S->graphs.size(), GBX_ERR_INVALID_INDEX, "unknown graph id");
     *lanes = S->graphs[graph_id].lanes;
+    return GBX_OK;
+}
+
+extern "C" gbx_status gbx_server_set_graph_desc(gbx_server* srv, int32_t graph_id, const gbx_desc* desc) {
+    clear_error();
+    GBX_CHECK(srv != nullptr && desc != nullptr, GBX_ERR_NULL_POINTER, "NULL argument");
+    Server* S = reinterpret_cast<Server*>(srv);
+    std::lock_guard<std::mutex> lock(S->mu);
+    GBX_CHECK(graph_id >= 0 && graph_id < (int32_t)S->graphs.size(), GBX_ERR_INVALID_INDEX, "unknown graph id");
+    const gbx_desc& d = *desc;
+    GBX_CHECK(d.direction >= GBX_DIR_AUTO && d.direction <= GBX_DIR_PULL, GBX_ERR_INVALID_VALUE, "desc.direction");
+    GBX_CHECK(d.alpha >= 0.0f && d.alpha == d.alpha, GBX_ERR_INVALID_VALUE, "desc.alpha must be >= 0");
+    GBX_CHECK(d.pull_probe == 0 || (d.pull_probe >= 4 && d.pull_probe <= 1024), GBX_ERR_INVALID_VALUE,
+              "desc.pull_probe must be 0 or in [4, 1024]");
+    GBX_CHECK(d.push_sort == 0, GBX_ERR_NOT_SUPPORTED, "desc.push_sort applies to gbx_mxv only");
+    gbx_desc keep = d;
+    keep.trace = 0;  // batches of the server are not traced
+    S->graphs[graph_id].desc = keep;
     return GBX_OK;
 }
 

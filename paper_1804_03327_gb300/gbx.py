@@ -57,7 +57,7 @@ EXPORTED = [
     "gbx_mxv_pull_noalloc", "gbx_bfs_batch", "gbx_bfs_batch_trace",
     "gbx_server_config_init", "gbx_server_create", "gbx_server_add_graph", "gbx_server_graph_lanes",
     "gbx_server_submit", "gbx_server_poll", "gbx_server_stats", "gbx_server_destroy", "gbx_autotune",
-    "gbx_graph_set_weights", "gbx_graph_copy_weights", "gbx_sssp", "gbx_sssp_trace",
+    "gbx_graph_set_weights", "gbx_graph_copy_weights", "gbx_sssp", "gbx_sssp_trace", "gbx_server_set_graph_desc",
 ]
 
 
@@ -144,6 +144,7 @@ def load():
                 "gbx_server_create": (ctypes.c_int, [ctypes.POINTER(p), ctypes.POINTER(ServerConfig)]),
                 "gbx_server_add_graph": (ctypes.c_int, [p, p, ctypes.POINTER(i32)]),
                 "gbx_server_graph_lanes": (ctypes.c_int, [p, i32, ctypes.POINTER(i32)]),
+                "gbx_server_set_graph_desc": (ctypes.c_int, [p, i32, ctypes.POINTER(Desc)]),
                 "gbx_server_submit": (ctypes.c_int, [p, i32, i32, p, u64]),
                 "gbx_server_poll": (ctypes.c_int, [p, ctypes.POINTER(Completion), i32, ctypes.POINTER(i32)]),
                 "gbx_server_stats": (ctypes.c_int, [p, ctypes.POINTER(i64), ctypes.POINTER(i32),
@@ -447,6 +448,10 @@ class Server:
         x = ctypes.c_int32()
         _check(load().gbx_server_graph_lanes(self._h, gid, ctypes.byref(x)), "gbx_server_graph_lanes")
         return x.value
+
+    def set_graph_desc(self, gid: int, desc: Desc):
+        """Descriptor of this graph's batches (e.g. from autotune(..., TUNE_BATCH, ...))."""
+        _check(load().gbx_server_set_graph_desc(self._h, gid, ctypes.byref(desc)), "gbx_server_set_graph_desc")
 
     def submit(self, gid: int, source: int, out, tag: int) -> bool:
         """Queue a query; False if the server refused it (queue full)."""

@@ -115,3 +115,33 @@ def test_server_memory_budget_limits_lanes():
         srv.add_graph(g)
     assert e.value.status == gbx.ERR_OUT_OF_MEMORY
     srv.destroy()
+
+
+def test_server_per_graph_descriptor():
+    """Batches of a graph run with the descriptor set for it (here: pull only on the
+    grid, push only on the RMAT graph); results stay equal to the oracle's."""
+    gs = graphs()
+    srv = gbx.Server(max_batch=64, slots=2)
+    ids = {nm: srv.add_graph(gs[nm][4]) for nm in ("rmat12", "grid")}
+    srv.set_graph_desc(ids["grid"], gbx.desc_init(direction=gbx.DIR_PULL, pull_probe=4))
+    srv.set_graph_desc(ids["rmat12"], gbx.desc_init(direction=gbx.DIR_PUSH))
+    with pytest.raises(gbx.GbxError) as e:
+        srv.set_graph_desc(99, gbx.desc_init())
+    assert e.value.status == gbx.ERR_INVALID_INDEX
+    with pytest.raises(gbx.GbxError) as e:
+        srv.set_graph_desc(ids["grid"], gbx.desc_init(pull_probe=2))
+    assert e.value.status == gbx.ERR_INVALID_VALUE
+    jobs, outs = [], []
+    for k in range(100):
+        nm = ("rmat12", "grid")[k % 2]
+        n, s, d, og, g = gs[nm]
+        src = int(synth.sources(n, s, d, 20, seed=11)[k % 20])
+        out = torch.full((n,), 5, dtype=torch.int32, device="cuda")
+        assert srv.submit(ids[nm], src, out, tag=k)
+        jobs.append((nm, src))
+        outs.append(out)
+    got = drain(srv, len(jobs))
+    assert all(c.status == 0 for c in got.values())
+    for k, (nm, src) in enumerate(jobs):
+        assert np.array_equal(outs[k].cpu().numpy(), oracle.bfs(gs[nm][3], src)[0])
+    srv.destroy()
