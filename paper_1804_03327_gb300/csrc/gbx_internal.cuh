@@ -145,7 +145,13 @@ struct Graph {
     cudaEvent_t ev_done[2] = {nullptr, nullptr};
     cudaEvent_t ev_copied[2] = {nullptr, nullptr};
     int bfs_blocks = 0;  // BFS launch geometry
+    // gbx_mxv launch sequences captured as CUDA graphs (keyed by the call's buffers and descriptor)
+    cudaStream_t mxv_cap_stream = nullptr;
+    struct MxvCache* mxv_cache = nullptr;
 };
+
+// Releases the captured gbx_mxv graphs of G (mxv.cu).
+void mxv_cache_release(Graph* G);
 
 // ---------------------------------------------------------------- primitives (prims.cu)
 

@@ -189,6 +189,7 @@ static void graph_release(Graph* g) {
         if (g->ev_copied[i]) cudaEventDestroy(g->ev_copied[i]);
     }
     if (g->copy_stream) cudaStreamDestroy(g->copy_stream);
+    mxv_cache_release(g);
     delete g;
 }
 

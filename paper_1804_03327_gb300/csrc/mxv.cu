@@ -11,6 +11,10 @@
 //     the radix sort of Algorithm 3).
 // The result bitmap is then written out as a dense byte vector or as a sorted
 // index list (Section 3: sparse vectors are sorted lists).
+#include <cstring>
+#include <new>
+#include <vector>
+
 #include "gbx_internal.cuh"
 
 namespace gbx {
@@ -377,6 +381,10 @@ static gbx_status build_pass(Graph* G, const gbx_vector* mask, int complement, c
 
 gbx_status mxv_minplus(Graph* G, float* w, const uint32_t* pass_bm, bool nothing_passes, const float* u,
                        const gbx_desc& d, cudaStream_t s);
+gbx_status mxv_issue(Graph* G, gbx_vector* w, const gbx_vector* mask, int32_t semiring, const gbx_vector* u,
+                     const gbx_desc& d, cudaStream_t s);
+gbx_status mxv_replay(Graph* G, gbx_vector* w, const gbx_vector* mask, int32_t semiring, const gbx_vector* u,
+                      const gbx_desc& d, cudaStream_t s);
 
 }  // namespace gbx
 
@@ -406,11 +414,29 @@ extern "C" gbx_status gbx_mxv(gbx_vector* w, const gbx_vector* mask, int32_t sem
     GBX_CHECK(d.push_sort == 0 || d.push_sort == 1, GBX_ERR_INVALID_VALUE, "desc.push_sort must be 0 or 1");
     for (int k = 0; k < 2; ++k) GBX_CHECK(d.reserved[k] == 0, GBX_ERR_INVALID_VALUE, "desc.reserved must be 0");
     GBX_CHECK(!mask || mask->format != GBX_DENSE_F32, GBX_ERR_INVALID_VALUE, "mask: GBX_DENSE or GBX_SPARSE");
-    cudaStream_t s = (cudaStream_t)stream;
     if (semiring == GBX_MIN_PLUS_F32) {
         GBX_CHECK(u->format == GBX_DENSE_F32 && w->format == GBX_DENSE_F32, GBX_ERR_INVALID_VALUE,
                   "the (min, +) semiring takes GBX_DENSE_F32 u and w");
         GBX_CHECK(d.push_sort == 0, GBX_ERR_NOT_SUPPORTED, "desc.push_sort is for the Boolean semiring");
+        GBX_CHECK(G->out_val != nullptr, GBX_ERR_INVALID_VALUE,
+                  "the (min, +) semiring needs edge weights (gbx_graph_set_weights)");
+    } else {
+        GBX_CHECK(u->format != GBX_DENSE_F32 && w->format != GBX_DENSE_F32, GBX_ERR_INVALID_VALUE,
+                  "GBX_DENSE_F32 vectors belong to the (min, +) semiring");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    // the sorted push reads the frontier size on the host: issued directly; every
+    // other call is one fixed launch sequence, replayed from a captured graph
+    if (d.push_sort) return mxv_issue(G, w, mask, semiring, u, d, s);
+    return mxv_replay(G, w, mask, semiring, u, d, s);
+}
+
+namespace gbx {
+
+gbx_status mxv_issue(Graph* G, gbx_vector* w, const gbx_vector* mask, int32_t semiring, const gbx_vector* u,
+                     const gbx_desc& d, cudaStream_t s) {
+    const int32_t n = G->n;
+    if (semiring == GBX_MIN_PLUS_F32) {
         const uint32_t* pbm = nullptr;
         bool none = false;
         GBX_TRY(build_pass(G, mask, d.mask_complement, &pbm, &none, s));
@@ -418,8 +444,6 @@ extern "C" gbx_status gbx_mxv(gbx_vector* w, const gbx_vector* mask, int32_t sem
         G->ws.last_stream = s;
         return GBX_OK;
     }
-    GBX_CHECK(u->format != GBX_DENSE_F32 && w->format != GBX_DENSE_F32, GBX_ERR_INVALID_VALUE,
-              "GBX_DENSE_F32 vectors belong to the (min, +) semiring");
 
     // w = A' u with A' = A^T (transpose) or A.  Pull reads rows of A' (CSR of A'),
     // push reads the columns of A' selected by u, i.e. rows of (A')^T.
@@ -530,6 +554,118 @@ extern "C" gbx_status gbx_mxv(gbx_vector* w, const gbx_vector* mask, int32_t sem
     G->ws.last_stream = s;
     return GBX_OK;
 }
+
+// ---------------------------------------------------------------- captured launch sequences
+
+// A gbx_mxv call with the same graph, buffers, counts' addresses, semiring and
+// descriptor issues the same kernels with the same arguments (counts and
+// contents are read on the device), so its launch sequence is captured once, on
+// a private stream, into a CUDA graph and replayed on the caller's stream.  The
+// most recently used kMxvGraphs sequences are kept per graph.
+constexpr size_t kMxvGraphs = 32;
+
+struct MxvKey {
+    const void* wd;
+    const void* wn;
+    const void* md;
+    const void* mn;
+    const void* ud;
+    const void* un;
+    int32_t wf, wc, mf, mc, uf, uc, has_mask, semiring;
+    gbx_desc d;
+};
+
+struct MxvCache {
+    struct Entry {
+        MxvKey key;
+        cudaGraphExec_t exec;
+        uint64_t used;
+    };
+    std::vector<Entry> entries;
+    uint64_t clock = 0;
+};
+
+static MxvKey make_key(const gbx_vector* w, const gbx_vector* mask, int32_t semiring, const gbx_vector* u,
+                       const gbx_desc& d) {
+    MxvKey k;
+    std::memset(&k, 0, sizeof(k));
+    k.wd = w->data;
+    k.wn = w->format == GBX_SPARSE ? w->nnz : nullptr;
+    k.wf = w->format;
+    k.wc = w->format == GBX_SPARSE ? w->capacity : 0;
+    if (mask) {
+        k.has_mask = 1;
+        k.md = mask->data;
+        k.mn = mask->format == GBX_SPARSE ? mask->nnz : nullptr;
+        k.mf = mask->format;
+        k.mc = mask->format == GBX_SPARSE ? mask->capacity : 0;
+    }
+    k.ud = u->data;
+    k.un = u->format == GBX_SPARSE ? u->nnz : nullptr;
+    k.uf = u->format;
+    k.uc = u->format == GBX_SPARSE ? u->capacity : 0;
+    k.semiring = semiring;
+    k.d = d;
+    return k;
+}
+
+void mxv_cache_release(Graph* G) {
+    if (G->mxv_cache) {
+        for (auto& e : G->mxv_cache->entries) cudaGraphExecDestroy(e.exec);
+        delete G->mxv_cache;
+        G->mxv_cache = nullptr;
+    }
+    if (G->mxv_cap_stream) {
+        cudaStreamDestroy(G->mxv_cap_stream);
+        G->mxv_cap_stream = nullptr;
+    }
+}
+
+gbx_status mxv_replay(Graph* G, gbx_vector* w, const gbx_vector* mask, int32_t semiring, const gbx_vector* u,
+                      const gbx_desc& d, cudaStream_t s) {
+    if (!G->mxv_cache) {
+        G->mxv_cache = new (std::nothrow) MxvCache();
+        GBX_CHECK(G->mxv_cache != nullptr, GBX_ERR_OUT_OF_MEMORY, "host allocation failed");
+    }
+    MxvCache& C = *G->mxv_cache;
+    const MxvKey key = make_key(w, mask, semiring, u, d);
+    for (auto& e : C.entries)
+        if (std::memcmp(&e.key, &key, sizeof(key)) == 0) {
+            e.used = ++C.clock;
+            GBX_CUDA_TRY(cudaGraphLaunch(e.exec, s));
+            G->ws.last_stream = s;
+            return GBX_OK;
+        }
+    if (!G->mxv_cap_stream) GBX_CUDA_TRY(cudaStreamCreateWithFlags(&G->mxv_cap_stream, cudaStreamNonBlocking));
+    cudaStream_t cs = G->mxv_cap_stream;
+    GBX_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    const gbx_status st = mxv_issue(G, w, mask, semiring, u, d, cs);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t ie = cudaErrorUnknown;
+    if (st == GBX_OK && ce == cudaSuccess && graph) ie = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (st != GBX_OK || ce != cudaSuccess || ie != cudaSuccess) {
+        // not capturable here: issue the sequence directly on the caller's stream
+        if (exec) cudaGraphExecDestroy(exec);
+        cudaGetLastError();
+        return mxv_issue(G, w, mask, semiring, u, d, s);
+    }
+    if (C.entries.size() >= kMxvGraphs) {
+        size_t lru = 0;
+        for (size_t i = 1; i < C.entries.size(); ++i)
+            if (C.entries[i].used < C.entries[lru].used) lru = i;
+        cudaGraphExecDestroy(C.entries[lru].exec);
+        C.entries.erase(C.entries.begin() + (long)lru);
+    }
+    C.entries.push_back({key, exec, ++C.clock});
+    GBX_CUDA_TRY(cudaGraphLaunch(exec, s));
+    G->ws.last_stream = s;
+    return GBX_OK;
+}
+
+}  // namespace gbx
 
 extern "C" gbx_status gbx_mxv_stats(const gbx_graph* A, int64_t* rows, int64_t* examined, int64_t* u_nnz,
                                     int64_t* edges) {
