@@ -115,6 +115,21 @@ def dist_env():
     return rank, world, local
 
 
+def aggregate_over_ranks(elapsed: float, edges: int, dist_mod=None, device="cpu"):
+    """Whole-job numbers of a weak-scaling run: the longest timed region over the
+    ranks (max) and the edges all ranks traversed (sum).  dist_mod is
+    torch.distributed when running under torchrun, else None (one rank)."""
+    if dist_mod is None:
+        return float(elapsed), int(edges)
+    import torch
+
+    t = torch.tensor([float(elapsed)], dtype=torch.float64, device=device)
+    e = torch.tensor([int(edges)], dtype=torch.int64, device=device)
+    dist_mod.all_reduce(t, op=dist_mod.ReduceOp.MAX)
+    dist_mod.all_reduce(e, op=dist_mod.ReduceOp.SUM)
+    return float(t.item()), int(e.item())
+
+
 def rank_sources(n, src, dst, rank: int, k: int = SOURCES, seed: int = SEED):
     """Sources of one rank: rank 0 takes the workload's 64 seeded sources; rank r
     takes 64 more from the seeded stream (weak scaling: fixed work per GPU)."""
@@ -823,14 +838,10 @@ def run_ours(args):
     torch.cuda.synchronize()
     clock_info = clocks.stop()
     gbx.graph_sync(g)
-    elapsed = t_start.elapsed_time(t_end) / 1e3
-    if dist:
-        t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed, total_edges = aggregate_over_ranks(t_start.elapsed_time(t_end) / 1e3, step_edges * args.steps,
+                                                dist if dist else None, "cuda")
     launch_ms = np.array([[a.elapsed_time(b) for (a, b) in evs[i]] for i in range(args.steps)])
     mean_launch_s = float(launch_ms.mean()) / 1e3
-    total_edges = step_edges * args.steps * world
     value = total_edges / elapsed / 1e9
 
     # verify the timed outputs against the traced pass (depth is deterministic)
@@ -864,12 +875,9 @@ def run_ours(args):
         t0 = time.perf_counter()
         for _ in range(e_steps):
             gbx.bfs_host(g, sources, dh, ph, desc)
-        e_el = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([e_el], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_el = float(t.item())
-        e2e = {"value": step_edges * e_steps * world / e_el / 1e9, "unit": UNIT,
+        e_el, e_edges = aggregate_over_ranks(time.perf_counter() - t0, step_edges * e_steps,
+                                             dist if dist else None, "cuda")
+        e2e = {"value": e_edges / e_el / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": 4 * S, "d2h_bytes_per_step": 2 * 4 * n * S,
                "steps": e_steps, "api": "gbx_bfs_host (pinned host depth+parent, D2H overlapped with the next BFS)"}
 
