@@ -243,8 +243,9 @@ __device__ __forceinline__ void ms_pull_commit(const MsArgs& a, const int32_t* l
 // with an atomicOr on V[v]; the lanes it gained (not set before) are new at level
 // L + 1 and this edge is their only claimant, so it writes their depth and ORs them
 // into F_next[v]; the first edge to gain anything at v lists v (for W == 1 the
-// previous F_next word tells, otherwise the T_next bit).  The plain probe of V[v]
-// only saves atomics (bits are only ever set), the atomic decides.
+// previous F_next word tells, otherwise the T_next bit).  One-word batches claim
+// without probing V[v] first (a dependent load per edge costs more than the extra
+// atomics); wider ones probe, which only saves reductions (bits are only ever set).
 template <int CW>
 __device__ __forceinline__ void ms_push(const MsArgs& a, int32_t L, const int32_t* q, const int32_t* qp,
                                         const int32_t* qd, uint32_t qcount, uint32_t qedges,
@@ -289,7 +290,7 @@ __device__ __forceinline__ void ms_push(const MsArgs& a, int32_t L, const int32_
 #pragma unroll
                         for (int j = 0; j < CW; ++j) {
                             const size_t iu = (size_t)u * a.W + c + j, iv = (size_t)v * a.W + c + j;
-                            const unsigned long long cand = Fc[iu] & ~a.V[iv];
+                            const unsigned long long cand = Fc[iu];
                             if (!cand) continue;
                             const unsigned long long old = atomicOr(a.V + iv, cand);
                             const unsigned long long gained = cand & ~old;
