@@ -20,8 +20,9 @@
  *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
  *    default stream).  Device work is enqueued on it and the call returns
  *    without synchronising unless its comment says otherwise.  Work on one
- *    graph handle uses that handle's scratch memory, so calls on the same
- *    graph must be ordered (one stream, or explicit events).
+ *    graph handle uses that handle's scratch memory (and the launch sequences
+ *    gbx_mxv keeps for it), so calls on the same graph must be ordered (one
+ *    stream, or explicit events) and issued by one host thread at a time.
  *  - Device pointers are plain CUDA device addresses (for example the
  *    data_ptr() of a CUDA tensor); host pointers are ordinary addresses.
  *  - Indices are int32; a graph holds fewer than 2^31 stored edges.
@@ -213,6 +214,10 @@ void gbx_desc_init(gbx_desc* d);
  * trip.  u, mask and w may be DENSE or SPARSE; a SPARSE w receives sorted
  * indices and its count in *w->nnz.  All vectors live in device memory and
  * must have size == n.  w must not alias u or mask.  Asynchronous on `stream`.
+ * A call's launch sequence depends only on the graph, the vectors' buffers and
+ * count addresses, the semiring and the descriptor; it is captured once into a
+ * CUDA graph and replayed for later calls with the same ones (the 32 most
+ * recent per graph are kept; push_sort calls are issued directly).
  * Errors: NULL_POINTER, NOT_SUPPORTED (semiring), DIMENSION_MISMATCH,
  * INVALID_VALUE (format, capacity < size for a SPARSE output, desc fields).
  *
