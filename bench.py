@@ -486,8 +486,10 @@ def run_sssp(args):
     srcs = [int(x) for x in synth.sources(n, src, dst, 16, seed=SEED + 7)]
     dist = torch.empty(n, dtype=torch.float32, device="cuda")
     rows = []
+    tuned, _ = gbx.autotune(g, gbx.TUNE_SSSP, synth.sources(n, src, dst, 8, seed=SEED + 9))
     modes = [("auto (alpha 0.01, beta 0.01)", gbx.desc_init()), ("two-phase (beta 0)", gbx.desc_init(beta=0.0)),
-             ("push only", gbx.desc_init(direction=gbx.DIR_PUSH)), ("pull only", gbx.desc_init(direction=gbx.DIR_PULL))]
+             ("push only", gbx.desc_init(direction=gbx.DIR_PUSH)), ("pull only", gbx.desc_init(direction=gbx.DIR_PULL)),
+             ("autotuned on 8 other sources", tuned)]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for label, desc in modes:
         relaxed, its, byts, sched = 0, 0, 0, None
@@ -528,7 +530,7 @@ def run_sssp(args):
            "sources": len(srcs), "peak": peak, "peak_kind": peak_kind, "rows": rows,
            "cpu_baseline": {"ms_per_sssp": tc * 1e3, "iterations": oit, "cores": 1, "kind": "oracle",
                             "sample": "first source, Jacobi Bellman-Ford in binary32"},
-           "first_source_equals_oracle": same}
+           "first_source_equals_oracle": same, "tuned_descriptor": gbx.desc_dict(tuned)}
     print(json.dumps(out), flush=True)
     g.free()
 

@@ -379,6 +379,7 @@ gbx_status gbx_bfs_batch_trace(gbx_graph* g, gbx_level* levels, int32_t cap, int
 
 #define GBX_TUNE_BFS 0   /* single-source gbx_bfs, timed over `count` separate runs */
 #define GBX_TUNE_BATCH 1 /* gbx_bfs_batch with the `count` sources as one batch */
+#define GBX_TUNE_SSSP 2  /* gbx_sssp, timed over `count` separate runs (the graph needs weights) */
 
 /*
  * Time candidate descriptors on g with the given host sources and return the
@@ -387,7 +388,8 @@ gbx_status gbx_bfs_batch_trace(gbx_graph* g, gbx_level* levels, int32_t cap, int
  * level; here whole descriptors are compared: for GBX_TUNE_BFS the direction
  * rule (ratio / Beamer) x alpha x beta, then the pull probe depth and the
  * persistent blocks per SM; for GBX_TUNE_BATCH the batch alpha, then the probe
- * depth.  Results never change (every candidate computes the same depths).  If
+ * depth; for GBX_TUNE_SSSP alpha x beta (beta 0: two phases), push only and pull
+ * only.  Results never change (every candidate computes the same output).  If
  * cache_path is not NULL, a previous result for the same graph shape (n, nnz,
  * symmetric, kind, batch size) is returned from that text file without timing,
  * and new results are appended to it.  Synchronises `stream`.  Allocates a

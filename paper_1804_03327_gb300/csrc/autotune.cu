@@ -64,7 +64,8 @@ extern "C" gbx_status gbx_autotune(gbx_graph* g, int32_t kind, const int32_t* so
                                    double* best_ms, const char* cache_path, void* stream) {
     clear_error();
     GBX_TRY(check_graph(g));
-    GBX_CHECK(kind == GBX_TUNE_BFS || kind == GBX_TUNE_BATCH, GBX_ERR_INVALID_VALUE, "unknown tuning kind");
+    GBX_CHECK(kind == GBX_TUNE_BFS || kind == GBX_TUNE_BATCH || kind == GBX_TUNE_SSSP, GBX_ERR_INVALID_VALUE,
+              "unknown tuning kind");
     GBX_CHECK(count >= 1 && sources != nullptr && best != nullptr, GBX_ERR_NULL_POINTER,
               "sources and best are required, count >= 1");
     Graph* G = as_impl(g);
@@ -101,18 +102,37 @@ extern "C" gbx_status gbx_autotune(gbx_graph* g, int32_t kind, const int32_t* so
                 cand.push_back(d);
             }
         }
-    } else {
+    } else if (kind == GBX_TUNE_BATCH) {
         const float alphas[] = {0.002f, 0.005f, 0.01f, 0.02f, 0.05f, 0.1f, 0.2f, 0.5f, 1e30f};
         for (float a : alphas) {
             gbx_desc d = base;
             d.alpha = a;
             cand.push_back(d);
         }
+    } else {
+        // SSSP: the switch rule on the improved-set size (beta = 0 keeps the two
+        // phases of Section 5.6), push only and pull only
+        const float alphas[] = {0.002f, 0.01f, 0.05f, 0.2f};
+        const float betas[] = {0.0f, 0.01f};
+        for (float b : betas)
+            for (float a : alphas) {
+                gbx_desc d = base;
+                d.alpha = a;
+                d.beta = b;
+                cand.push_back(d);
+            }
+        gbx_desc d = base;
+        d.direction = GBX_DIR_PUSH;
+        cand.push_back(d);
+        d.direction = GBX_DIR_PULL;
+        cand.push_back(d);
     }
     // buffers
+    if (kind == GBX_TUNE_SSSP)
+        GBX_CHECK(G->out_val != nullptr, GBX_ERR_INVALID_VALUE, "GBX_TUNE_SSSP needs edge weights");
     void* depth = nullptr;
-    const size_t bytes = kind == GBX_TUNE_BFS ? sizeof(int32_t) * (size_t)G->n
-                                              : sizeof(int16_t) * (size_t)G->n * (size_t)count;
+    const size_t bytes = kind == GBX_TUNE_BATCH ? sizeof(int16_t) * (size_t)G->n * (size_t)count
+                                                : sizeof(int32_t) * (size_t)G->n;  // int32 depths or float distances
     GBX_CUDA_TRY(cudaMallocAsync(&depth, bytes, s));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     gbx_status st = GBX_OK;
@@ -120,6 +140,10 @@ extern "C" gbx_status gbx_autotune(gbx_graph* g, int32_t kind, const int32_t* so
         if (kind == GBX_TUNE_BFS) {
             for (int32_t k = 0; k < count; ++k)
                 GBX_TRY(gbx_bfs(g, sources[k], static_cast<int32_t*>(depth), nullptr, &d, stream));
+            return GBX_OK;
+        }
+        if (kind == GBX_TUNE_SSSP) {
+            for (int32_t k = 0; k < count; ++k) GBX_TRY(gbx_sssp(g, sources[k], static_cast<float*>(depth), &d, stream));
             return GBX_OK;
         }
         return gbx_bfs_batch(g, sources, count, depth, GBX_DEPTH_I16, &d, stream);
@@ -169,7 +193,7 @@ extern "C" gbx_status gbx_autotune(gbx_graph* g, int32_t kind, const int32_t* so
     const int32_t probes_bfs[] = {8, 32};
     const int32_t probes_batch[] = {4, 16};
     const int32_t* probes = kind == GBX_TUNE_BFS ? probes_bfs : probes_batch;
-    for (int i = 0; i < 2 && st == GBX_OK; ++i) {
+    for (int i = 0; i < 2 && st == GBX_OK && kind != GBX_TUNE_SSSP; ++i) {
         gbx_desc d = winner;
         d.pull_probe = probes[i];
         double ms = 0.0;

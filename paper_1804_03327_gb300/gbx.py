@@ -49,6 +49,7 @@ DEPTH_I32 = 0
 DEPTH_I16 = 1
 TUNE_BFS = 0
 TUNE_BATCH = 1
+TUNE_SSSP = 2
 
 EXPORTED = [
     "gbx_last_error", "gbx_status_string", "gbx_version", "gbx_graph_build", "gbx_graph_free", "gbx_graph_info",

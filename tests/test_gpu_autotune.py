@@ -43,3 +43,21 @@ def test_autotune_batch():
     gbx.bfs_batch(g, srcs, depth, desc)
     gbx.graph_sync(g)
     assert np.array_equal(depth.cpu().numpy(), oracle.ms_bfs(og, srcs))
+
+
+def test_autotune_sssp():
+    n, s, d = synth.rmat_edges(12, 16, seed=56)
+    w = (np.arange(len(s)) % 13 + 1).astype(np.float32)
+    og = oracle.graph_weighted(n, s, d, w)
+    g = gbx.graph_build(n, s, d)
+    with pytest.raises(gbx.GbxError) as e:  # no weights yet
+        gbx.autotune(g, gbx.TUNE_SSSP, synth.sources(n, s, d, 4, seed=57))
+    assert e.value.status == gbx.ERR_INVALID_VALUE
+    gbx.graph_set_weights(g, s, d, w)
+    desc, ms = gbx.autotune(g, gbx.TUNE_SSSP, synth.sources(n, s, d, 4, seed=57))
+    assert ms > 0 and desc.direction in (gbx.DIR_AUTO, gbx.DIR_PUSH, gbx.DIR_PULL)
+    dist = torch.empty(n, dtype=torch.float32, device="cuda")
+    for src in synth.sources(n, s, d, 3, seed=58):
+        gbx.sssp(g, int(src), dist, desc)
+        gbx.graph_sync(g)
+        assert np.array_equal(dist.cpu().numpy(), oracle.sssp(og, int(src))[0])
