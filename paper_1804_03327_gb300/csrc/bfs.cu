@@ -146,6 +146,10 @@ __device__ __forceinline__ void push_level(const BfsArgs& a, int32_t L, int cur,
 #define GBX_PULL_ILP 2
 #endif
 constexpr int kPullIlp = GBX_PULL_ILP;  // candidate rows per lane per round (independent probe chains)
+#ifndef GBX_PULL_STEP
+#define GBX_PULL_STEP 2
+#endif
+constexpr int kPullStep = GBX_PULL_STEP;  // in-neighbours a lane loads per probe step (loads in flight)
 // Bitmap words one warp takes at a time in a pull level, a.tile_words: 32, 16 or
 // 8 (lane l holds word l of the tile).  The host picks the width whose round-robin
 // critical path, ceil(tiles / warps) * width, is shortest (ties: the wider), so a
@@ -293,18 +297,18 @@ __device__ __forceinline__ void pull_level(const BfsArgs& a, int32_t L, int vcur
                     }
                 }
             }
-            // lane probes: up to a.probe in-neighbours per row, four at a time, both rows in lockstep
-            for (int it = 0; it < a.probe / 4; ++it) {
-                int32_t jj[kPullIlp][4];
+            // lane probes: up to a.probe in-neighbours per row, kPullStep at a time, both rows in lockstep
+            for (int it = 0; it < (a.probe + kPullStep - 1) / kPullStep; ++it) {
+                int32_t jj[kPullIlp][kPullStep];
                 int32_t cnt[kPullIlp];
                 bool act[kPullIlp];
 #pragma unroll
                 for (int r = 0; r < kPullIlp; ++r) {
                     const int32_t lim = end[r] < beg[r] + a.probe ? end[r] : beg[r] + a.probe;
                     act[r] = mine[r] && !done[r] && k[r] < lim;
-                    cnt[r] = act[r] ? (lim - k[r] < 4 ? lim - k[r] : 4) : 0;
+                    cnt[r] = act[r] ? (lim - k[r] < kPullStep ? lim - k[r] : kPullStep) : 0;
 #pragma unroll
-                    for (int t = 0; t < 4; ++t) jj[r][t] = t < cnt[r] ? __ldg(a.in_col + k[r] + t) : 0;
+                    for (int t = 0; t < kPullStep; ++t) jj[r][t] = t < cnt[r] ? __ldg(a.in_col + k[r] + t) : 0;
                 }
                 bool any = false;
 #pragma unroll
@@ -315,13 +319,13 @@ __device__ __forceinline__ void pull_level(const BfsArgs& a, int32_t L, int vcur
                     if (!act[r]) continue;
                     int hit = -1;
 #pragma unroll
-                    for (int t = 3; t >= 0; --t)
+                    for (int t = kPullStep - 1; t >= 0; --t)
                         if (t < cnt[r] && bit_test(tbm, jj[r][t])) hit = t;
                     if (hit >= 0 && !found[r]) {
                         found[r] = true;
                         par[r] = jj[r][0];
 #pragma unroll
-                        for (int t = 1; t < 4; ++t)
+                        for (int t = 1; t < kPullStep; ++t)
                             if (hit == t) par[r] = jj[r][t];
                         if (a.early_exit) {
                             exam[r] += (unsigned long long)(hit + 1);
