@@ -70,6 +70,13 @@ def parse():
     p.add_argument("--repeat", type=int, default=5)
     p.add_argument("--probe-alpha", type=float, default=None, help="--probe descriptor: alpha (default 0.01)")
     p.add_argument("--probe-pull-probe", type=int, default=0, help="--probe descriptor: pull_probe")
+    p.add_argument("--probe-batch", type=int, default=None, metavar="S",
+                   help="profiling aid: the workload's first S sources as one batch with the autotuned batch "
+                        "descriptor, --repeat warm-up batches, then one batch between cudaProfilerStart/Stop "
+                        "(for ncu --profile-from-start off)")
+    p.add_argument("--probe-sssp", type=int, default=None, metavar="K",
+                   help="profiling aid: SSSP from the K-th source of the --sssp workload with its autotuned "
+                        "descriptor, --repeat warm-up runs, then one run between cudaProfilerStart/Stop")
     return p.parse_args()
 
 
@@ -106,6 +113,86 @@ def run_probe(args):
     print(json.dumps({"probe_sources": len(listed), "descriptor": kw,
                       "algorithmic_bytes_mean": float(np.mean(b_alg)),
                       "reached_edges": roofline.reached_edges(tr), **roofline.summary(tr)}))
+
+
+def profiled(fn):
+    """Run fn() once between cudaProfilerStart and cudaProfilerStop (what a profiler
+    started with profiling from the start off captures) and return its time in
+    seconds, taken with CUDA events in a separate uncaptured run before it."""
+    import torch
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    fn()
+    e1.record()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    fn()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def run_probe_batch(args):
+    """The batched line's first measurement in isolation: the workload's first S
+    sources as one batch (int16 depths) with the batch descriptor autotuned on S
+    other seeded sources, as the benchmark does; one batch is left for a profiler."""
+    import torch
+
+    import synth
+    from paper_1804_03327_gb300 import gbx, roofline
+
+    gbx.load()
+    n, src, dst = synth.rmat_edges(args.scale, EDGE_FACTOR, seed=SEED)
+    S = args.probe_batch
+    srcs = rank_sources(n, src, dst, 0, k=S)
+    g = gbx.graph_build(n, src, dst)
+    bdesc, _ = gbx.autotune(g, gbx.TUNE_BATCH, synth.sources(n, src, dst, S, seed=SEED + 200))
+    d1 = torch.empty(n, dtype=torch.int32, device="cuda")
+    reached = 0
+    for x in srcs:
+        gbx.bfs(g, int(x), d1, None, gbx.desc_init(trace=1))
+        reached += roofline.reached_edges(gbx.bfs_trace(g))
+    depth = torch.empty((S, n), dtype=torch.int16, device="cuda")
+    for _ in range(args.repeat):
+        gbx.bfs_batch(g, srcs, depth, bdesc)
+    t = profiled(lambda: gbx.bfs_batch(g, srcs, depth, bdesc))
+    gbx.graph_sync(g)
+    print(json.dumps({"probe_batch": S, "graph": f"rmat{args.scale}-ef{EDGE_FACTOR}", "descriptor": gbx.desc_dict(bdesc),
+                      "reached_edges": reached, "ms": t * 1e3, "gteps": reached / t / 1e9}))
+    g.free()
+
+
+def run_probe_sssp(args):
+    """One SSSP of the --sssp workload in isolation: source K of its 16 sources,
+    the descriptor autotuned on its 8 other sources; algorithmic bytes from a traced
+    run; one untraced run is left for a profiler."""
+    import torch
+
+    import synth
+    from paper_1804_03327_gb300 import gbx
+
+    gbx.load()
+    n, src, dst = synth.rmat_edges(args.scale, EDGE_FACTOR, seed=SEED)
+    w = np.random.default_rng(SEED).integers(1, 65, size=len(src)).astype(np.float32)
+    g = gbx.graph_build(n, src, dst)
+    gbx.graph_set_weights(g, src, dst, w)
+    x = int(synth.sources(n, src, dst, 16, seed=SEED + 7)[args.probe_sssp])
+    tuned, _ = gbx.autotune(g, gbx.TUNE_SSSP, synth.sources(n, src, dst, 8, seed=SEED + 9))
+    dist = torch.empty(n, dtype=torch.float32, device="cuda")
+    d = gbx.Desc.from_buffer_copy(tuned)
+    d.trace = 1
+    gbx.sssp(g, x, dist, d)
+    tr = gbx.sssp_trace(g)
+    for _ in range(args.repeat):
+        gbx.sssp(g, x, dist, tuned)
+    t = profiled(lambda: gbx.sssp(g, x, dist, tuned))
+    gbx.graph_sync(g)
+    print(json.dumps({"probe_sssp": args.probe_sssp, "source": x, "descriptor": gbx.desc_dict(tuned),
+                      "iterations": len(tr), "relaxed_edges": int(tr["e_exam"].sum()),
+                      "algorithmic_bytes": sssp_bytes(tr, n), "ms": t * 1e3}))
+    g.free()
 
 
 def dist_env():
@@ -938,6 +1025,10 @@ def main():
     args = parse()
     if args.probe is not None:
         run_probe(args)
+    elif args.probe_batch is not None:
+        run_probe_batch(args)
+    elif args.probe_sssp is not None:
+        run_probe_sssp(args)
     elif args.sweep:
         run_sweep(args)
     elif args.ablation:

@@ -180,7 +180,10 @@ typedef struct {
     int32_t trace;           /* BFS: record per-level statistics (see gbx_bfs_trace) */
     int32_t pull_probe;      /* BFS pull: in-neighbours one lane scans before its warp takes the row over
                                 (0 = default: 16 single-source, 8 batched; otherwise 4..1024) */
-    int32_t blocks_per_sm;   /* BFS kernels: persistent blocks per SM (0 = as many as fit) */
+    int32_t blocks_per_sm;   /* BFS and SSSP kernels: persistent blocks per SM (0 = as many as fit).
+                                gbx_bfs_batch: 1 or 2 caps the default build (two per SM); 3 or more
+                                selects a register-lean build at three per SM for batches of at most
+                                128 sources run alone (server batches keep the default build) */
     int32_t push_sort;       /* gbx_mxv push: 1 = Algorithm 3 / Section 6.2 (gather the selected columns,
                                 key-only radix sort, segmented reduction, mask) instead of the one-pass
                                 bitmap claim; same result.  Takes the AUTO decision on the host (one
@@ -458,8 +461,9 @@ gbx_status gbx_server_graph_lanes(gbx_server* s, int32_t graph_id, int32_t* lane
 gbx_status gbx_server_set_graph_desc(gbx_server* s, int32_t graph_id, const gbx_desc* desc);
 /* Queue a BFS from `source` on graph `graph_id`; its depths (n entries of the
  * server's depth type, device memory, caller-owned, untouched until the query
- * completes) go to depth_out.  May start batches.  Errors: BUSY (queue full),
- * INVALID_INDEX, NULL_POINTER. */
+ * completes) go to depth_out.  The server's streams do not wait on the caller's:
+ * work of other streams on depth_out must have finished before the call.  May
+ * start batches.  Errors: BUSY (queue full), INVALID_INDEX, NULL_POINTER. */
 gbx_status gbx_server_submit(gbx_server* s, int32_t graph_id, int32_t source, void* depth_out, uint64_t tag);
 /* Collect finished batches, start new ones on free slots, and return up to max
  * completions (oldest first) in out; *nout receives how many. */

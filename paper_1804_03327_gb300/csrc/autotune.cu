@@ -203,6 +203,17 @@ extern "C" gbx_status gbx_autotune(gbx_graph* g, int32_t kind, const int32_t* so
             winner = d;
         }
     }
+    // batches of at most 128 sources: the register-lean build at three blocks per SM
+    if (kind == GBX_TUNE_BATCH && st == GBX_OK && count <= 128) {
+        gbx_desc d = winner;
+        d.blocks_per_sm = 3;
+        double ms = 0.0;
+        st = time_desc(d, &ms);
+        if (st == GBX_OK && ms < win_ms) {
+            win_ms = ms;
+            winner = d;
+        }
+    }
     if (kind == GBX_TUNE_BFS && st == GBX_OK && G->bfs_blocks > 1) {
         gbx_desc d = winner;
         d.blocks_per_sm = G->bfs_blocks - 1;

@@ -31,6 +31,14 @@
 namespace gbx {
 
 constexpr int kMsThreads = 512;
+// Register budgets of the persistent batched kernel: the default build fits two
+// 512-thread blocks on an SM (64 registers a thread: twice the resident warps of an
+// unbounded build at 114, for 24-222 bytes of spills), the lean build three (40
+// registers, more spills; lane words 1 and 2 only).  Lean pays on graphs with few
+// wide levels and loses on long chains of small ones (a grid), so a descriptor
+// chooses it (blocks_per_sm >= 3) and the autotuner times both.
+constexpr int kMsOcc = 2;
+constexpr int kMsOccLean = 3;
 constexpr int kMsProbe = 8;  // default in-neighbours a lane scans alone before the warp takes over
 
 struct MsArgs {
@@ -387,8 +395,8 @@ __device__ __forceinline__ void ms_clear_prev(const MsArgs& a, const int32_t* id
 
 // ---------------------------------------------------------------- kernel
 
-template <int CW>
-__global__ void __launch_bounds__(kMsThreads, 1) ms_bfs_kernel(MsArgs a) {
+template <int CW, int kOcc>
+__global__ void __launch_bounds__(kMsThreads, kOcc) ms_bfs_kernel(MsArgs a) {
     const long long gtid = (long long)blockIdx.x * kMsThreads + threadIdx.x;
     // an error of an earlier launch not yet read by the host: this launch does nothing
     const int pending = threadIdx.x == 0 ? ld_volatile_i32(a.status + ST_ERROR) : 0;
@@ -598,16 +606,18 @@ int64_t ms_scratch_bytes(int32_t n, int32_t S) {
     return 4ll * 8ll * (int64_t)n * ((w_raw + cw - 1) / cw * cw) + 4ll * ((int64_t)n + 1);
 }
 
-template <int CW>
-static gbx_status ms_launch(Graph* G, const MsArgs& a0, int blocks, cudaStream_t s) {
+template <int CW, int kOcc>
+static gbx_status ms_launch(Graph* G, const MsArgs& a0, int blocks, int per_sm_cap, cudaStream_t s) {
     int per_sm = 0;
-    GBX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ms_bfs_kernel<CW>, kMsThreads, 0));
+    GBX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ms_bfs_kernel<CW, kOcc>, kMsThreads, 0));
     GBX_CHECK(per_sm >= 1, GBX_ERR_CUDA, "batched BFS kernel cannot be resident");
+    if (per_sm_cap > 0 && per_sm_cap < per_sm) per_sm = per_sm_cap;
     const int full = per_sm * G->num_sms;
     const int nb = blocks > 1 ? (full / blocks > 0 ? full / blocks : 1) : full;  // a 1/blocks share of the GPU
     MsArgs a = a0;
     void* args[] = {&a};
-    GBX_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)ms_bfs_kernel<CW>, dim3(nb), dim3(kMsThreads), args, 0, s));
+    GBX_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)ms_bfs_kernel<CW, kOcc>, dim3(nb), dim3(kMsThreads), args, 0,
+                                             s));
     return GBX_OK;
 }
 
@@ -662,8 +672,17 @@ gbx_status ms_run(Graph* G, Workspace& w, int32_t S, const int32_t* src_dev, voi
     a.trace_cap = kTraceCap;
     a.probe = d.pull_probe > 0 ? d.pull_probe : kMsProbe;
     a.timeout_ns = wait_timeout_ns();
-    const gbx_status st = cw == 4 ? ms_launch<4>(G, a, blocks, s)
-                                  : (cw == 2 ? ms_launch<2>(G, a, blocks, s) : ms_launch<1>(G, a, blocks, s));
+    // the lean build only when this batch has the GPU to itself: concurrent cooperative
+    // grids of one register budget tile the SMs exactly, mixed budgets need not
+    const bool lean = blocks <= 1 && d.blocks_per_sm >= kMsOccLean && cw <= 2;
+    const int cap = lean ? 0 : d.blocks_per_sm;
+    gbx_status st;
+    if (cw == 4)
+        st = ms_launch<4, kMsOcc>(G, a, blocks, cap, s);
+    else if (cw == 2)
+        st = lean ? ms_launch<2, kMsOccLean>(G, a, blocks, cap, s) : ms_launch<2, kMsOcc>(G, a, blocks, cap, s);
+    else
+        st = lean ? ms_launch<1, kMsOccLean>(G, a, blocks, cap, s) : ms_launch<1, kMsOcc>(G, a, blocks, cap, s);
     if (st != GBX_OK) return st;
     w.bar_parity ^= 1u;
     w.last_stream = s;
@@ -695,6 +714,7 @@ extern "C" gbx_status gbx_bfs_batch(gbx_graph* g, const int32_t* sources, int32_
     GBX_CHECK(d.pull_probe == 0 || (d.pull_probe >= 4 && d.pull_probe <= 1024), GBX_ERR_INVALID_VALUE,
               "desc.pull_probe must be 0 or in [4, 1024]");
     GBX_CHECK(d.push_sort == 0, GBX_ERR_NOT_SUPPORTED, "desc.push_sort applies to gbx_mxv only");
+    GBX_CHECK(d.blocks_per_sm >= 0, GBX_ERR_INVALID_VALUE, "desc.blocks_per_sm must be >= 0");
     cudaStream_t s = (cudaStream_t)stream;
     GBX_TRY(ms_reserve(G->ws, G->n, S, s));
     if (G->ws.ms_src_cap < S) {

@@ -276,6 +276,7 @@ extern "C" gbx_status gbx_server_set_graph_desc(gbx_server* srv, int32_t graph_i
     GBX_CHECK(d.pull_probe == 0 || (d.pull_probe >= 4 && d.pull_probe <= 1024), GBX_ERR_INVALID_VALUE,
               "desc.pull_probe must be 0 or in [4, 1024]");
     GBX_CHECK(d.push_sort == 0, GBX_ERR_NOT_SUPPORTED, "desc.push_sort applies to gbx_mxv only");
+    GBX_CHECK(d.blocks_per_sm >= 0, GBX_ERR_INVALID_VALUE, "desc.blocks_per_sm must be >= 0");
     gbx_desc keep = d;
     keep.trace = 0;  // batches of the server are not traced
     S->graphs[graph_id].desc = keep;

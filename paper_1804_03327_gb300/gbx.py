@@ -455,7 +455,8 @@ class Server:
         _check(load().gbx_server_set_graph_desc(self._h, gid, ctypes.byref(desc)), "gbx_server_set_graph_desc")
 
     def submit(self, gid: int, source: int, out, tag: int) -> bool:
-        """Queue a query; False if the server refused it (queue full)."""
+        """Queue a query; False if the server refused it (queue full).  The server's
+        streams do not wait on torch's: work queued on `out` must have finished."""
         st = load().gbx_server_submit(self._h, int(gid), int(source), out.data_ptr(), int(tag))
         if st == ERR_BUSY:
             return False

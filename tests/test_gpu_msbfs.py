@@ -87,25 +87,45 @@ def test_batch_then_single_source_share_scratch():
     assert np.array_equal(got2, got[:10])
 
 
+@pytest.mark.parametrize("name", ["rmat12", "rmat11-directed", "grid"])
+@pytest.mark.parametrize("S", [64, 100, 200])
+def test_batch_every_build_and_block_cap(name, S):
+    """blocks_per_sm 1 and 2 cap the default build, 3 and more select the
+    register-lean build (at most 128 sources); every choice gives the oracle's
+    depths in each direction."""
+    n, s, d, og, g = graph(name)
+    srcs = synth.sources(n, s, d, S, seed=S + 11)
+    want = oracle.ms_bfs(og, srcs)
+    for bps in (1, 2, 3, 7):
+        for direction in (gbx.DIR_AUTO, gbx.DIR_PUSH, gbx.DIR_PULL):
+            got = run_batch(g, n, srcs, gbx.desc_init(direction=direction, blocks_per_sm=bps))
+            assert np.array_equal(got, want), (bps, direction)
+        tr = gbx.bfs_batch_trace(g)
+        assert len(tr) == want.max() + 1 and tr["n_new"].sum() == np.sum(want > 0)
+
+
 def test_batch_rejects_bad_arguments():
     n, s, d, og, g = graph("rmat12")
     depth = torch.empty((2, n), dtype=torch.int32, device="cuda")
     with pytest.raises(gbx.GbxError) as e:
         gbx.bfs_batch(g, [0, n], depth)
     assert e.value.status == gbx.ERR_INVALID_INDEX
+    with pytest.raises(gbx.GbxError) as e:
+        gbx.bfs_batch(g, [0, 1], depth, gbx.desc_init(blocks_per_sm=-1))
+    assert e.value.status == gbx.ERR_INVALID_VALUE
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("S", [64, 1024])
-def test_full_size_rmat21_batch_sampled_lanes(S):
-    """RMAT scale 21 (edge factor 16) with S sources in one batch: sampled lanes
-    bit-exact against the oracle."""
+@pytest.mark.parametrize("S,bps", [(64, 0), (64, 3), (1024, 0)])
+def test_full_size_rmat21_batch_sampled_lanes(S, bps):
+    """RMAT scale 21 (edge factor 16) with S sources in one batch, default and
+    register-lean builds: sampled lanes bit-exact against the oracle."""
     n, s, d = synth.rmat_edges(21, 16, seed=1)
     og = oracle.graph(n, s, d)
     g = gbx.graph_build(n, s, d)
     srcs = synth.sources(n, s, d, S, seed=1)
     depth = torch.empty((S, n), dtype=torch.int16, device="cuda")
-    gbx.bfs_batch(g, srcs, depth)
+    gbx.bfs_batch(g, srcs, depth, gbx.desc_init(blocks_per_sm=bps))
     gbx.graph_sync(g)
     for b in sorted({0, 1, S // 2, S - 1}):
         assert np.array_equal(depth[b].cpu().numpy().astype(np.int32), oracle.bfs(og, srcs[b])[0])

@@ -26,6 +26,19 @@ def graphs():
     return _graphs
 
 
+def filled_all(sizes, value, dtype=None):
+    """Depth buffers pre-filled with a sentinel.  The fills run on torch's stream
+    and the server's streams do not wait on it, so they must have finished before
+    a buffer is submitted (one synchronisation, then the submissions back to back)."""
+    outs = [torch.full((n,), value, dtype=dtype or torch.int32, device="cuda") for n in sizes]
+    torch.cuda.synchronize()
+    return outs
+
+
+def filled(n, value, dtype=None):
+    return filled_all([n], value, dtype)[0]
+
+
 def drain(srv, want, timeout=60.0):
     got = {}
     t0 = time.time()
@@ -44,7 +57,7 @@ def test_server_results_alone_equal_results_in_the_mix():
     # alone
     n0, s0, d0, og0, g0 = gs["rmat12"]
     probe_src = int(synth.sources(n0, s0, d0, 1, seed=99)[0])
-    alone = torch.full((n0,), 555, dtype=torch.int32, device="cuda")
+    alone = filled(n0, 555)
     assert srv.submit(gid["rmat12"], probe_src, alone, tag=10**9)
     c = drain(srv, 1)[10**9]
     assert c.status == 0 and c.batch_size == 1
@@ -59,12 +72,9 @@ def test_server_results_alone_equal_results_in_the_mix():
         src = int(synth.sources(n, s, d, 40, seed=k % 7)[rng.integers(0, 40)])
         jobs.append((nm, src))
     jobs.insert(180, ("rmat12", probe_src))
-    outs = []
+    outs = filled_all([gs[nm][0] for nm, _ in jobs], 777)
     for tag, (nm, src) in enumerate(jobs):
-        n = gs[nm][0]
-        out = torch.full((n,), 777, dtype=torch.int32, device="cuda")
-        outs.append(out)
-        assert srv.submit(gid[nm], src, out, tag=tag)
+        assert srv.submit(gid[nm], src, outs[tag], tag=tag)
     got = drain(srv, len(jobs))
     assert all(c.status == 0 for c in got.values())
     assert max(c.batch_size for c in got.values()) > 1  # queries were batched
@@ -87,8 +97,9 @@ def test_server_int16_rows_and_admission():
     srcs = synth.sources(n, s, d, 40, seed=3)
     outs, accepted = [], 0
     refused = 0
+    bufs = filled_all([n] * len(srcs), 9, torch.int16)
     for k, src in enumerate(srcs):
-        out = torch.full((n,), 9, dtype=torch.int16, device="cuda")
+        out = bufs[k]
         if srv.submit(gid, int(src), out, tag=k):
             outs.append((k, src, out))
             accepted += 1
@@ -131,15 +142,14 @@ def test_server_per_graph_descriptor():
     with pytest.raises(gbx.GbxError) as e:
         srv.set_graph_desc(ids["grid"], gbx.desc_init(pull_probe=2))
     assert e.value.status == gbx.ERR_INVALID_VALUE
-    jobs, outs = [], []
+    jobs = []
     for k in range(100):
         nm = ("rmat12", "grid")[k % 2]
         n, s, d, og, g = gs[nm]
-        src = int(synth.sources(n, s, d, 20, seed=11)[k % 20])
-        out = torch.full((n,), 5, dtype=torch.int32, device="cuda")
-        assert srv.submit(ids[nm], src, out, tag=k)
-        jobs.append((nm, src))
-        outs.append(out)
+        jobs.append((nm, int(synth.sources(n, s, d, 20, seed=11)[k % 20])))
+    outs = filled_all([gs[nm][0] for nm, _ in jobs], 5)
+    for k, (nm, src) in enumerate(jobs):
+        assert srv.submit(ids[nm], src, outs[k], tag=k)
     got = drain(srv, len(jobs))
     assert all(c.status == 0 for c in got.values())
     for k, (nm, src) in enumerate(jobs):
