@@ -683,7 +683,8 @@ def batched_measurements(g, n, sources, reached, single_value, args):
         torch.cuda.synchronize()
         gbx.graph_sync(gg)
         del depth
-        return e0.elapsed_time(e1) / reps / 1e3
+        tuned = {k: gbx.desc_dict(bdesc)[k] for k in ("alpha", "pull_probe", "blocks_per_sm")}
+        return e0.elapsed_time(e1) / reps / 1e3, tuned
 
     def reached_of(gg, srcs, nn):
         # reached undirected edges per source, from one traced single-source BFS each
@@ -697,12 +698,12 @@ def batched_measurements(g, n, sources, reached, single_value, args):
 
     res = {}
     import synth as _synth
-    t = time_batch(g, sources, n, tune_srcs=_synth.sources(n, *args._edges, len(sources), seed=SEED + 200))
+    t, tuned = time_batch(g, sources, n, tune_srcs=_synth.sources(n, *args._edges, len(sources), seed=SEED + 200))
     v = sum(reached) / t / 1e9
     import oracle
     og_main = oracle_graph(n, *args._edges)
     res["same_sources_as_one_batch"] = {"workload": WORKLOAD, "S": len(sources), "ms": t * 1e3, "value": v,
-                                        "unit": UNIT, "vs_single_source": v / single_value,
+                                        "unit": UNIT, "vs_single_source": v / single_value, "descriptor": tuned,
                                         "cpu_baseline": cpu_parallel_oracle([(og_main, sources, reached)])}
     cfg4 = []
     for name, gen in [("rmat21-ef16", lambda: synth.rmat_edges(21, EDGE_FACTOR, seed=SEED)),
@@ -726,11 +727,12 @@ def batched_measurements(g, n, sources, reached, single_value, args):
         import oracle
         cpu_b = cpu_parallel_oracle([(oracle_graph(nn, ss, dd), all_src[:64], reach[:64])])
         for S in widths:
-            tb = time_batch(gg, all_src[:S], nn, reps=1 if name.startswith("grid") else 3, tune_srcs=tune_all[:S])
+            tb, tuned = time_batch(gg, all_src[:S], nn, reps=1 if name.startswith("grid") else 3,
+                                   tune_srcs=tune_all[:S])
             edges = sum(reach[:S])
             cfg4.append({"graph": name, "S": S, "ms": tb * 1e3, "value": edges / tb / 1e9, "unit": UNIT,
                          "single_source_value": edges / (single_s * S) / 1e9,
-                         "speedup_vs_single_source": single_s * S / tb, "cpu_baseline": cpu_b})
+                         "speedup_vs_single_source": single_s * S / tb, "descriptor": tuned, "cpu_baseline": cpu_b})
         gg.free()
     res["configs"] = cfg4
     return res
