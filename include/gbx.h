@@ -181,9 +181,9 @@ typedef struct {
     int32_t pull_probe;      /* BFS pull: in-neighbours one lane scans before its warp takes the row over
                                 (0 = default: 16 single-source, 8 batched; otherwise 4..1024) */
     int32_t blocks_per_sm;   /* BFS and SSSP kernels: persistent blocks per SM (0 = as many as fit).
-                                gbx_bfs_batch: 1 or 2 caps the default build (two per SM); 3 or more
-                                selects a register-lean build at three per SM for batches of at most
-                                128 sources run alone (server batches keep the default build) */
+                                gbx_bfs_batch and gbx_sssp: 1 or 2 caps the default build (two per
+                                SM); 3 or more selects a register-lean build at three per SM (batches:
+                                at most 128 sources run alone; server batches keep the default build) */
     int32_t push_sort;       /* gbx_mxv push: 1 = Algorithm 3 / Section 6.2 (gather the selected columns,
                                 key-only radix sort, segmented reduction, mask) instead of the one-pass
                                 bitmap claim; same result.  Takes the AUTO decision on the host (one

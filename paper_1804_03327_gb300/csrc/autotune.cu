@@ -203,8 +203,8 @@ extern "C" gbx_status gbx_autotune(gbx_graph* g, int32_t kind, const int32_t* so
             winner = d;
         }
     }
-    // batches of at most 128 sources: the register-lean build at three blocks per SM
-    if (kind == GBX_TUNE_BATCH && st == GBX_OK && count <= 128) {
+    // batches of at most 128 sources and SSSP: the register-lean build at three blocks per SM
+    if (((kind == GBX_TUNE_BATCH && count <= 128) || kind == GBX_TUNE_SSSP) && st == GBX_OK) {
         gbx_desc d = winner;
         d.blocks_per_sm = 3;
         double ms = 0.0;

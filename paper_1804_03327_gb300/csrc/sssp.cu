@@ -17,6 +17,14 @@
 namespace gbx {
 
 constexpr int kSsspThreads = 512;
+// Register budgets: the default build fits two 512-thread blocks on an SM (64
+// registers, no spills), the lean build three (40 registers, ~200 bytes of spills).
+// Lean hides more gather latency on push iterations over a skewed graph (RMAT-22
+// push only: 2.61 -> 2.28 ms) and loses where pull iterations or many small ones
+// dominate (the direction rule on RMAT-22 3.27 -> 4.89 ms, a 1024x1024 grid +16 %),
+// so a descriptor chooses it (blocks_per_sm >= 3) and the autotuner times it.
+constexpr int kSsspOcc = 2;
+constexpr int kSsspOccLean = 3;
 
 struct SsspArgs {
     int32_t n, nwords, source;
@@ -148,8 +156,8 @@ __device__ __forceinline__ void sssp_chg_to_queue(const SsspArgs& a, Stage& st) 
     st.flush();
 }
 
-template <bool kTrace>
-__global__ void __launch_bounds__(kSsspThreads, 2) sssp_kernel(SsspArgs a) {
+template <bool kTrace, int kOcc>
+__global__ void __launch_bounds__(kSsspThreads, kOcc) sssp_kernel(SsspArgs a) {
     const long long gtid = (long long)blockIdx.x * kSsspThreads + threadIdx.x;
     const long long gstride = (long long)gridDim.x * kSsspThreads;
     const int32_t s = a.source;
@@ -323,11 +331,14 @@ extern "C" gbx_status gbx_sssp(gbx_graph* g, int32_t source, float* dist, const 
     a.trace_cap = kTraceCap;
     a.timeout_ns = wait_timeout_ns();
     a.bar_parity = w.bar_parity;
-    const void* fn = d.trace ? (const void*)sssp_kernel<true> : (const void*)sssp_kernel<false>;
+    const bool lean = d.blocks_per_sm >= kSsspOccLean;
+    const void* fn = lean ? (d.trace ? (const void*)sssp_kernel<true, kSsspOccLean>
+                                     : (const void*)sssp_kernel<false, kSsspOccLean>)
+                          : (d.trace ? (const void*)sssp_kernel<true, kSsspOcc> : (const void*)sssp_kernel<false, kSsspOcc>);
     int per_sm = 0;
     GBX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kSsspThreads, 0));
     GBX_CHECK(per_sm >= 1, GBX_ERR_CUDA, "SSSP kernel cannot be resident");
-    if (d.blocks_per_sm > 0 && d.blocks_per_sm < per_sm) per_sm = d.blocks_per_sm;
+    if (!lean && d.blocks_per_sm > 0 && d.blocks_per_sm < per_sm) per_sm = d.blocks_per_sm;
     void* args[] = {&a};
     GBX_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(per_sm * G->num_sms), dim3(kSsspThreads), args, 0, s));
     w.bar_parity ^= 1u;

@@ -139,10 +139,13 @@ def test_sssp_matches_oracle_every_direction(name, integer):
     for src in synth.sources(n, s, d, 3, seed=6):
         want, _ = oracle.sssp(og, int(src))
         for desc in [gbx.desc_init(), gbx.desc_init(beta=0.0), gbx.desc_init(direction=gbx.DIR_PUSH),
-                     gbx.desc_init(direction=gbx.DIR_PULL), gbx.desc_init(alpha=0.0005)]:
+                     gbx.desc_init(direction=gbx.DIR_PULL), gbx.desc_init(alpha=0.0005),
+                     gbx.desc_init(blocks_per_sm=1), gbx.desc_init(blocks_per_sm=3),
+                     gbx.desc_init(direction=gbx.DIR_PUSH, blocks_per_sm=3)]:
             gbx.sssp(g, int(src), dist, desc)
             gbx.graph_sync(g)
-            assert np.array_equal(dist.cpu().numpy(), want), (name, src, desc.direction, desc.alpha, desc.beta)
+            assert np.array_equal(dist.cpu().numpy(), want), (name, src, desc.direction, desc.alpha, desc.beta,
+                                                              desc.blocks_per_sm)
 
 
 def test_sssp_unit_weights_equal_bfs_depth_and_trace():
@@ -151,9 +154,9 @@ def test_sssp_unit_weights_equal_bfs_depth_and_trace():
     gbx.graph_set_weights(g, s, d, np.ones(len(s), np.float32))
     og = oracle.graph(n, s, d)
     dist = torch.zeros(n, dtype=torch.float32, device="cuda")
-    for src in synth.sources(n, s, d, 3, seed=7):
+    for k, src in enumerate(synth.sources(n, s, d, 3, seed=7)):
         depth, _, _ = oracle.bfs(og, int(src))
-        gbx.sssp(g, int(src), dist, gbx.desc_init(trace=1))
+        gbx.sssp(g, int(src), dist, gbx.desc_init(trace=1, blocks_per_sm=3 if k == 1 else 0))  # k = 1: lean build
         tr = gbx.sssp_trace(g)
         want = np.where(depth >= 0, depth.astype(np.float32), np.float32(np.inf))
         assert np.array_equal(dist.cpu().numpy(), want)
