@@ -434,7 +434,8 @@ typedef struct {
     uint64_t tag;
     int32_t graph_id;
     int32_t source;
-    int32_t status;     /* GBX_OK, or the device-side error of its batch */
+    int32_t status;     /* GBX_OK, or the error of its batch: recorded on the device, or of its
+                           launch (a batch that cannot be launched completes at once) */
     int32_t levels;     /* levels of its batch (max over the batch's lanes) */
     int32_t batch_size; /* queries in its batch */
     int32_t reserved;

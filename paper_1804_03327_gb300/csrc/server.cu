@@ -117,7 +117,22 @@ static gbx_status reap(Server* S) {
     return GBX_OK;
 }
 
-// Start batches on free slots, oldest waiting graph first.
+// Copies a slot's staged sources and output rows, launches its batch and queues the
+// status read-back and the completion event, all on the slot's stream.
+static gbx_status launch_batch(Server* S, Slot& sl, const GraphEntry& ge, int32_t nb) {
+    GBX_CUDA_TRY(cudaMemcpyAsync(sl.src_dev, sl.src_pinned, sizeof(int32_t) * nb, cudaMemcpyHostToDevice, sl.stream));
+    GBX_CUDA_TRY(cudaMemcpyAsync(sl.rows_dev, sl.rows_pinned, sizeof(void*) * nb, cudaMemcpyHostToDevice, sl.stream));
+    GBX_TRY(ms_run(ge.g, sl.ws, nb, sl.src_dev, nullptr, sl.rows_dev, S->cfg.depth_type == GBX_DEPTH_I16 ? 1 : 0,
+                   ge.desc, (int)S->slots.size(), sl.stream));
+    GBX_CUDA_TRY(cudaMemcpyAsync(sl.status_pinned, sl.ws.status, sizeof(int32_t) * ST_WORDS, cudaMemcpyDeviceToHost,
+                                 sl.stream));
+    GBX_CUDA_TRY(cudaEventRecord(sl.done, sl.stream));
+    return GBX_OK;
+}
+
+// Start batches on free slots, oldest waiting graph first.  A batch whose launch
+// fails completes at once: each of its queries gets a completion carrying the error
+// (and gbx_last_error its message), so no accepted query is ever dropped.
 static gbx_status dispatch(Server* S) {
     for (Slot& sl : S->slots) {
         if (sl.busy) continue;
@@ -143,15 +158,26 @@ static gbx_status dispatch(Server* S) {
             sl.batch.push_back(qq);
         }
         S->queued -= nb;
-        GBX_CUDA_TRY(cudaMemcpyAsync(sl.src_dev, sl.src_pinned, sizeof(int32_t) * nb, cudaMemcpyHostToDevice, sl.stream));
-        GBX_CUDA_TRY(cudaMemcpyAsync(sl.rows_dev, sl.rows_pinned, sizeof(void*) * nb, cudaMemcpyHostToDevice, sl.stream));
-        const gbx_desc d = ge.desc;
         sl.t_launch = S->now();
-        GBX_TRY(ms_run(ge.g, sl.ws, nb, sl.src_dev, nullptr, sl.rows_dev, S->cfg.depth_type == GBX_DEPTH_I16 ? 1 : 0,
-                       d, (int)S->slots.size(), sl.stream));
-        GBX_CUDA_TRY(cudaMemcpyAsync(sl.status_pinned, sl.ws.status, sizeof(int32_t) * ST_WORDS,
-                                     cudaMemcpyDeviceToHost, sl.stream));
-        GBX_CUDA_TRY(cudaEventRecord(sl.done, sl.stream));
+        const gbx_status st = launch_batch(S, sl, ge, nb);
+        if (st != GBX_OK) {
+            const double t = S->now();
+            for (const Query& qq : sl.batch) {
+                gbx_completion c = {};
+                c.tag = qq.tag;
+                c.graph_id = qq.graph;
+                c.source = qq.source;
+                c.status = st;
+                c.levels = 0;
+                c.batch_size = nb;
+                c.t_submit = qq.t_submit;
+                c.t_launch = sl.t_launch;
+                c.t_done = t;
+                S->done.push_back(c);
+            }
+            sl.batch.clear();
+            continue;
+        }
         sl.graph = best;
         sl.busy = true;
     }
