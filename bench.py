@@ -74,6 +74,10 @@ def parse():
                    help="profiling aid: the workload's first S sources as one batch with the autotuned batch "
                         "descriptor, --repeat warm-up batches, then one batch between cudaProfilerStart/Stop "
                         "(for ncu --profile-from-start off)")
+    p.add_argument("--probe-mxv", action="store_true",
+                   help="profiling aid: one masked pull matvec (dense frontier of density 0.2, half the rows "
+                        "unvisited, early exit) and one push matvec (sparse frontier of density 0.001) on the "
+                        "workload graph, each between cudaProfilerStart/Stop after warm-up")
     p.add_argument("--probe-sssp", type=int, default=None, metavar="K",
                    help="profiling aid: SSSP from the K-th source of the --sssp workload with its autotuned "
                         "descriptor, --repeat warm-up runs, then one run between cudaProfilerStart/Stop")
@@ -161,6 +165,47 @@ def run_probe_batch(args):
     gbx.graph_sync(g)
     print(json.dumps({"probe_batch": S, "graph": f"rmat{args.scale}-ef{EDGE_FACTOR}", "descriptor": gbx.desc_dict(bdesc),
                       "reached_edges": reached, "ms": t * 1e3, "gteps": reached / t / 1e9}))
+    g.free()
+
+
+def run_probe_mxv(args):
+    """The standalone masked matvec w = A^T u .* !m on the workload graph, once in
+    each direction, with algorithmic bytes from the call's own work counters (the
+    byte model of --sweep)."""
+    import torch
+
+    import synth
+    from paper_1804_03327_gb300 import gbx
+
+    gbx.load()
+    n, src, dst = synth.rmat_edges(args.scale, EDGE_FACTOR, seed=SEED)
+    g = gbx.graph_build(n, src, dst)
+    vis = torch.from_numpy(synth.vertex_set(n, 0.5, seed=SEED + 1)).cuda()
+    w = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    out = {"probe_mxv": f"rmat{args.scale}-ef{EDGE_FACTOR}", "calls": []}
+    for label, fd, direction in (("pull", 0.2, gbx.DIR_PULL), ("push", 0.001, gbx.DIR_PUSH)):
+        u8 = torch.from_numpy(synth.vertex_set(n, fd, seed=SEED)).cuda()
+        idx = torch.nonzero(u8).flatten().to(torch.int32)
+        ulist = torch.zeros(n, dtype=torch.int32, device="cuda")
+        ulist[: idx.numel()] = idx
+        ucnt = torch.tensor([idx.numel()], dtype=torch.int32, device="cuda")
+        uvec = gbx.dense(u8) if direction == gbx.DIR_PULL else gbx.sparse(ulist, ucnt, n)
+        desc = gbx.desc_init(direction=direction, early_exit=1, mask_complement=1, trace=1)
+        gbx.mxv(gbx.dense(w), gbx.dense(vis), gbx.LOR_LAND, g, uvec, desc)
+        st = gbx.mxv_stats(g)
+        desc.trace = 0
+        for _ in range(args.repeat):
+            gbx.mxv(gbx.dense(w), gbx.dense(vis), gbx.LOR_LAND, g, uvec, desc)
+        t = profiled(lambda: gbx.mxv(gbx.dense(w), gbx.dense(vis), gbx.LOR_LAND, g, uvec, desc))
+        vec = n if direction == gbx.DIR_PULL else 4 * int(idx.numel())
+        if direction == gbx.DIR_PUSH:
+            alg = 12 * st["u_nnz"] + 4 * st["edges"] + n // 8 * 2
+        else:
+            alg = 8 * st["rows"] + 4 * st["examined"] + n // 8 * 3
+        alg += vec + 2 * n  # u, the dense mask, the dense output
+        out["calls"].append({"direction": label, "frontier_density": fd, "unvisited_density": 0.5, "stats": st,
+                             "algorithmic_bytes": alg, "ms": t * 1e3})
+    print(json.dumps(out))
     g.free()
 
 
@@ -1031,6 +1076,8 @@ def main():
         run_probe_batch(args)
     elif args.probe_sssp is not None:
         run_probe_sssp(args)
+    elif args.probe_mxv:
+        run_probe_mxv(args)
     elif args.sweep:
         run_sweep(args)
     elif args.ablation:
