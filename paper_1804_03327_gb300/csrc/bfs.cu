@@ -882,14 +882,29 @@ extern "C" gbx_status gbx_bfs_host(gbx_graph* g, const int32_t* sources, int32_t
     cudaStream_t s = (cudaStream_t)stream;
     const size_t bytes = sizeof(int32_t) * (size_t)G->n;
     if (!G->copy_stream) {
-        GBX_CUDA_TRY(cudaStreamCreateWithFlags(&G->copy_stream, cudaStreamNonBlocking));
-        for (int i = 0; i < 2; ++i) {
-            GBX_CUDA_TRY(cudaMalloc((void**)&G->hdepth[i], bytes));
-            GBX_CUDA_TRY(cudaMalloc((void**)&G->hparent[i], bytes));
-            GBX_CUDA_TRY(cudaEventCreateWithFlags(&G->ev_done[i], cudaEventDisableTiming));
-            GBX_CUDA_TRY(cudaEventCreateWithFlags(&G->ev_copied[i], cudaEventDisableTiming));
-            GBX_CUDA_TRY(cudaEventRecord(G->ev_copied[i], G->copy_stream));
+        // all or nothing: a partial setup would leave null buffers behind a live copy stream
+        cudaStream_t cs = nullptr;
+        int32_t* buf[4] = {nullptr, nullptr, nullptr, nullptr};  // depth 0, 1, parent 0, 1
+        cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // done 0, 1, copied 0, 1
+        cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaMalloc((void**)&buf[i], bytes);
+        for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+        for (int i = 2; i < 4 && e == cudaSuccess; ++i) e = cudaEventRecord(ev[i], cs);
+        if (e != cudaSuccess) {
+            for (int i = 0; i < 4; ++i) {
+                if (buf[i]) cudaFree(buf[i]);
+                if (ev[i]) cudaEventDestroy(ev[i]);
+            }
+            if (cs) cudaStreamDestroy(cs);
+            GBX_CUDA_TRY(e);
         }
+        for (int i = 0; i < 2; ++i) {
+            G->hdepth[i] = buf[i];
+            G->hparent[i] = buf[2 + i];
+            G->ev_done[i] = ev[i];
+            G->ev_copied[i] = ev[2 + i];
+        }
+        G->copy_stream = cs;
     }
     for (int32_t k = 0; k < count; ++k) {
         const int b = k & 1;
