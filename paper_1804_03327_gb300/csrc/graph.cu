@@ -193,10 +193,9 @@ static void graph_release(Graph* g) {
     delete g;
 }
 
-gbx_status workspace_alloc(Workspace& w, int32_t n) {
+static gbx_status workspace_alloc_all(Workspace& w, int32_t n) {
     const size_t nw = (size_t)(n + 31) / 32 + 1;
     const size_t nn = (size_t)n + 1;
-    w.n_cap = n;
     for (auto& p : w.bm) GBX_CUDA_TRY(cudaMalloc((void**)&p, sizeof(uint32_t) * nw));
     for (int i = 0; i < 2; ++i) {
         GBX_CUDA_TRY(cudaMalloc((void**)&w.q[i], sizeof(int32_t) * nn));
@@ -213,7 +212,16 @@ gbx_status workspace_alloc(Workspace& w, int32_t n) {
     GBX_CUDA_TRY(cudaMemset(w.status, 0, sizeof(int32_t) * ST_WORDS));
     GBX_CUDA_TRY(cudaMalloc((void**)&w.flag, sizeof(int32_t) * 64));
     GBX_CUDA_TRY(cudaMemset(w.flag, 0, sizeof(int32_t) * 64));
+    w.n_cap = n;  // only once every buffer exists
     return GBX_OK;
+}
+
+// All or nothing: a failed allocation releases what was allocated, so no half-built
+// workspace (one that claims capacity n but holds null buffers) is ever left behind.
+gbx_status workspace_alloc(Workspace& w, int32_t n) {
+    const gbx_status st = workspace_alloc_all(w, n);
+    if (st != GBX_OK) workspace_release(w);
+    return st;
 }
 
 static gbx_status build_impl(Graph* g, int32_t n, int64_t m, const int32_t* src, const int32_t* dst, uint32_t flags,
