@@ -85,13 +85,18 @@ extern "C" gbx_status gbx_graph_set_weights(gbx_graph* g, int64_t m, const int32
     if (!on_device)
         for (int64_t e = 0; e < m; ++e) GBX_CHECK(std::isfinite(w[e]), GBX_ERR_INVALID_VALUE, "weights must be finite");
     const int64_t nnz = G->nnz;
-    if (!G->out_val) {
-        GBX_CUDA_TRY(cudaMalloc((void**)&G->out_val, sizeof(float) * (size_t)(nnz > 0 ? nnz : 1)));
-        if (G->symmetric) {
-            G->in_val = G->out_val;
-        } else {
-            GBX_CUDA_TRY(cudaMalloc((void**)&G->in_val, sizeof(float) * (size_t)(nnz > 0 ? nnz : 1)));
+    if (!G->out_val) {  // both orientations or neither: a half-made pair would leave in_val null
+        const size_t bytes = sizeof(float) * (size_t)(nnz > 0 ? nnz : 1);
+        float* ov = nullptr;
+        float* iv = nullptr;
+        cudaError_t e = cudaMalloc((void**)&ov, bytes);
+        if (e == cudaSuccess && !G->symmetric) e = cudaMalloc((void**)&iv, bytes);
+        if (e != cudaSuccess) {
+            if (ov) cudaFree(ov);
+            GBX_CUDA_TRY(e);
         }
+        G->out_val = ov;
+        G->in_val = G->symmetric ? ov : iv;
     }
     const float inf = INFINITY;
     if (nnz > 0) {
