@@ -337,7 +337,9 @@ gbx_status gbx_bfs_trace(gbx_graph* g, gbx_level* levels, int32_t cap, int32_t* 
  * the smallest left-to-right rounded path sum, independent of the schedule.
  * A negative cycle ends in GBX_ERR_OVERFLOW after n iterations (reported by
  * gbx_graph_sync).  One persistent cooperative launch, asynchronous on
- * `stream`.  Errors: NULL_POINTER, INVALID_INDEX, INVALID_VALUE (no weights,
+ * `stream`; desc->blocks_per_sm >= 3 selects a register-lean build at three
+ * blocks per SM (faster on long push iterations over skewed graphs, slower with
+ * pull iterations; GBX_TUNE_SSSP times both).  Errors: NULL_POINTER, INVALID_INDEX, INVALID_VALUE (no weights,
  * desc fields), NOT_SUPPORTED (push_sort), CUDA.
  */
 gbx_status gbx_sssp(gbx_graph* g, int32_t source, float* dist, const gbx_desc* desc, void* stream);
@@ -363,11 +365,15 @@ gbx_status gbx_sssp_trace(gbx_graph* g, gbx_level* levels, int32_t cap, int32_t*
  * out-edges exceed desc->alpha * nnz, else push.  Sources may repeat.
  * sources: host int32[S] in [0, n).  depth: device buffer [S][n] of int32
  * (GBX_DEPTH_I32) or int16 (GBX_DEPTH_I16): depth[b][v] = hops from sources[b],
- * -1 if unreached -- each row equals gbx_bfs from that source.  Scratch (3 x n x
- * ceil(S/64) uint64) is allocated on the first call and kept by the graph.
+ * -1 if unreached -- each row equals gbx_bfs from that source.  Scratch (4 x n x W
+ * uint64, W = ceil(S/64) rounded up to a multiple of the word chunk 1, 2 or 4, plus
+ * int32[n+1]) is allocated on the first call and kept by the graph, grown when a
+ * wider batch comes.  desc->blocks_per_sm >= 3 with S <= 128 selects a register-lean
+ * build of the kernel at three blocks per SM (faster on skewed graphs with few wide
+ * levels, slower on long chains of small ones; GBX_TUNE_BATCH times both).
  * Asynchronous on `stream`; device-side errors are reported by gbx_graph_sync.
  * Errors: NULL_POINTER, INVALID_VALUE (S < 1, depth_type, desc), INVALID_INDEX,
- * OUT_OF_MEMORY, CUDA.
+ * NOT_SUPPORTED (push_sort), OUT_OF_MEMORY, CUDA.
  */
 gbx_status gbx_bfs_batch(gbx_graph* g, const int32_t* sources, int32_t S, void* depth, int32_t depth_type,
                          const gbx_desc* desc, void* stream);
