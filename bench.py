@@ -493,9 +493,59 @@ def run_sweep(args):
                                                     for r in res if r["f"] == fd])) for fd in fdens}
         out["graphs"][name] = {"points": res, "pull_beats_push_from_frontier_density": cross,
                                "push_sort_time_over_push_time": sort_ratio,
-                               "best_gbs": best, "best_frac": best / peak}
+                               "best_gbs": best, "best_frac": best / peak,
+                               "structured": sweep_structured(g, n, src, dst, w, e0, e1)}
         g.free()
     print(json.dumps(out), flush=True)
+
+
+def sweep_structured(g, n, src, dst, w, e0, e1, max_levels=24):
+    """The sweep's structured mode: the operator on the vectors a real BFS produces
+    instead of random ones.  One BFS from a seeded source gives the depths; for a
+    level L the frontier u is the set at depth L and the mask the vertices at depth
+    <= L (complemented), i.e. the inputs of level L + 1's matvec.  Push and masked
+    pull with early exit are timed on each of up to max_levels levels spread evenly
+    over the BFS (dense u), with the random sweep's byte model."""
+    import torch
+
+    import synth
+    from paper_1804_03327_gb300 import gbx
+
+    s = int(synth.sources(n, src, dst, 1, seed=SEED + 5)[0])
+    depth = torch.empty(n, dtype=torch.int32, device="cuda")
+    gbx.bfs(g, s, depth, None)
+    gbx.graph_sync(g)
+    levels = int(depth.max().item()) + 1
+    picked = sorted({int(x) for x in np.linspace(0, levels - 1, min(max_levels, levels)).round()})
+    rows = []
+    for L in picked:
+        u8 = (depth == L).to(torch.uint8)
+        vis = ((depth >= 0) & (depth <= L)).to(torch.uint8)
+        row = {"level": L, "f": int(u8.sum().item()) / n, "m_unvisited": 1.0 - int(vis.sum().item()) / n}
+        for label, direction in (("push", gbx.DIR_PUSH), ("pull_early_exit", gbx.DIR_PULL)):
+            desc = gbx.desc_init(direction=direction, early_exit=1, mask_complement=1, trace=1)
+            gbx.mxv(gbx.dense(w), gbx.dense(vis), gbx.LOR_LAND, g, gbx.dense(u8), desc)  # work counters, untimed
+            st = gbx.mxv_stats(g)
+            desc.trace = 0
+            gbx.mxv(gbx.dense(w), gbx.dense(vis), gbx.LOR_LAND, g, gbx.dense(u8), desc)  # warm-up
+            ts = []
+            for _ in range(3):
+                e0.record()
+                gbx.mxv(gbx.dense(w), gbx.dense(vis), gbx.LOR_LAND, g, gbx.dense(u8), desc)
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            t = float(np.median(ts)) / 1e3
+            if direction == gbx.DIR_PUSH:
+                alg = 12 * st["u_nnz"] + 4 * st["edges"] + n // 8 * 2
+            else:
+                alg = 8 * st["rows"] + 4 * st["examined"] + n // 8 * 3
+            alg += 3 * n  # dense u, the dense mask, the dense output
+            row[f"{label}_ms"] = t * 1e3
+            row[f"{label}_gbs"] = alg / t / 1e9
+        row["faster"] = "pull" if row["pull_early_exit_ms"] < row["push_ms"] else "push"
+        rows.append(row)
+    return {"source": s, "levels": levels, "points": rows}
 
 
 def run_ablation(args):
