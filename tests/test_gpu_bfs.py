@@ -4,6 +4,7 @@ Depths must match bit-exactly; parents must be valid (early exit and atomic
 claims may pick any parent); per-level counts and the direction schedule
 must match the oracle's trace and its Section 6.3 rule exactly."""
 import itertools
+import os
 
 import numpy as np
 import pytest
@@ -274,19 +275,27 @@ def test_bounded_wait_times_out_and_context_survives():
 
 
 @pytest.mark.slow
-def test_full_size_rmat22_sampled_sources():
-    """RMAT scale 22 (edge factor 16), in the launch configuration the benchmark
-    times: depths of sampled sources bit-exact against the oracle."""
+def test_full_size_rmat22_all_workload_sources():
+    """RMAT scale 22 (edge factor 16), the benchmark's 64 sources with the
+    descriptor the benchmark autotunes on 16 other sources: every source's depths
+    bit-exact against the oracle (run one source per host thread: ctypes releases
+    the GIL in the C BFS), parents valid on a sample."""
+    from concurrent.futures import ThreadPoolExecutor
+
     n, s, d = synth.rmat_edges(22, 16, seed=1)
     og = oracle.graph(n, s, d)
     g = gbx.graph_build(n, s, d)
     nn, nnz, _ = g.info()
     assert nnz == og.nnz
-    srcs = synth.sources(n, s, d, 64, seed=1)
-    for src in list(srcs[:3]) + [int(srcs[-1])]:
-        want, _, levels = oracle.bfs(og, src)
-        depth, parent = run_bfs(g, n, int(src))
-        assert np.array_equal(depth, want)
+    srcs = [int(x) for x in synth.sources(n, s, d, 64, seed=1)]
+    tuned, _ = gbx.autotune(g, gbx.TUNE_BFS, synth.sources(n, s, d, 16, seed=101))
+    with ThreadPoolExecutor(os.cpu_count() or 1) as ex:
+        wants = list(ex.map(lambda x: oracle.bfs(og, x)[0], srcs))
+    for k, src in enumerate(srcs):
+        depth, parent = run_bfs(g, n, src, tuned)
+        assert np.array_equal(depth, wants[k]), (k, src)
+        if k % 16:
+            continue
         # parents: check a seeded sample against the CSR
         reached = np.flatnonzero(depth > 0)
         pick = reached[np.random.default_rng(0).choice(len(reached), 2000, replace=False)]
