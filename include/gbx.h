@@ -142,7 +142,7 @@ gbx_status gbx_graph_sync(gbx_graph* g, void* stream);
 
 /* A non-owning view of a vector in device memory. */
 typedef struct {
-    int32_t format;   /* GBX_DENSE or GBX_SPARSE */
+    int32_t format;   /* GBX_DENSE, GBX_SPARSE or GBX_DENSE_F32 */
     int32_t size;     /* logical length; must equal the graph's n */
     void* data;       /* device pointer, layout per format */
     int32_t* nnz;     /* GBX_SPARSE: device pointer to the stored count (read for inputs,
