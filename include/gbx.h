@@ -157,7 +157,8 @@ typedef struct {
 #define GBX_DIR_PULL 2 /* row-based matvec (Eq 2/4, Algorithm 2) */
 
 #define GBX_HEUR_RATIO 0  /* Section 6.3: r = nnz(f)/M against alpha (up) and beta (down) */
-#define GBX_HEUR_BEAMER 1 /* Beamer's test that Section 6.3 starts from: nnz(m_f)/nnz(m_u) > alpha up */
+/* Beamer's test that Section 6.3 starts from: nnz(m_f)/nnz(m_u) > alpha up, nnz(f)/M < beta down */
+#define GBX_HEUR_BEAMER 1
 
 /*
  * Operation modifiers.  Section 6.3 carries the sparse/dense switch point

@@ -22,8 +22,10 @@ double, ``sssp`` as Bellman-Ford with binary32 sums) is in ``oracle.c`` too.
 Pins (tests/test_oracle_pins.py): brute-force dense Boolean matvec BFS on
 n <= 64, closed forms (grid Manhattan distance, path, star, complete graph),
 BFS invariants, scipy's BFS as an outside library, dense-matrix mxv for every
-flag combination, and the Figure 3 worked example (tests/golden/).  The
-(min, +) functions: weights against a Python dictionary of pairs; the matvec
+flag combination, the Figure 3 worked example and two hand-worked direction
+schedules, one per rule, plus a closed form of Beamer's rule on a path
+(tests/golden/).  The (min, +) functions: weights against a Python
+dictionary of pairs; the matvec
 against the Boolean oracle (zero weights), unit vectors (a column of weights)
 and tropical linearity; SSSP against scipy's Dijkstra (exact on integer
 weights), the BFS depth (unit weights) and the Bellman optimality conditions.
@@ -161,8 +163,10 @@ def direction_schedule(trace: np.ndarray, n: int, alpha: float = 0.01, beta: flo
     beamer rule (the test Section 6.3 starts from): push -> pull if
     m_f / m_u > alpha, with m_f the out-edges of F_{L+1} and m_u the in-edges of
     the vertices still unvisited after step L (no switch when m_u = 0);
-    pull -> push as in the ratio rule.  Thresholds are single precision, as the
-    descriptor carries them; comparisons are in double precision.
+    pull -> push if r_{L+1} < beta, with no condition on the frontier's trend
+    (Section 6.3 states Beamer's way back as nnz(f)/M < beta alone).
+    Thresholds are single precision, as the descriptor carries them;
+    comparisons are in double precision.
     """
     if mode in ("push", "pull"):
         return [mode] * len(trace)
@@ -185,7 +189,10 @@ def direction_schedule(trace: np.ndarray, n: int, alpha: float = 0.01, beta: flo
                 if mu > 0 and float(mf) / float(mu) > a:
                     d = "pull"
         else:
-            if r_new < b and nn < nf:
+            if heuristic == "ratio":
+                if r_new < b and nn < nf:
+                    d = "push"
+            elif r_new < b:
                 d = "push"
     return dirs
 

@@ -706,8 +706,9 @@ __global__ void __launch_bounds__(kBfsThreads, kBfsMinBlocks) bfs_kernel(BfsArgs
                     const long long mu_next = mu - in_new;
                     if (mu_next > 0 && (double)mf_new / (double)mu_next > (double)a.alpha) next = DIR_PULL;
                 }
-            } else {
-                if (r_new < (double)a.beta && n_new < nf) next = DIR_PUSH;
+            } else if (r_new < (double)a.beta && (a.heuristic != GBX_HEUR_RATIO || n_new < nf)) {
+                // the ratio rule also wants r decreasing; Beamer's way back is r < beta alone
+                next = DIR_PUSH;
             }
         }
         if (dir == DIR_PULL) vcur ^= 1;

@@ -268,6 +268,42 @@ def test_direction_rule_worked_example():
     assert oracle.direction_schedule(tr, ex["n"], mode="pull") == ["pull"] * len(tr)
 
 
+def test_direction_rule_beamer_worked_example():
+    """Beamer's edge test on a hand-worked graph: the trace fields the rule reads
+    (mf_new, mu) and the schedule; a step where m_f/m_u crosses alpha while the
+    frontier is still small, and pull levels that return to push although the
+    frontier did not shrink."""
+    ex = json.load(open(os.path.join(GOLDEN, "direction_rule_beamer_example.json")))
+    n = ex["n"]
+    e = np.array(ex["edges"], dtype=np.int32)
+    g = oracle.graph(n, e[:, 0], e[:, 1])
+    depth, _, levels = oracle.bfs(g, ex["source"])
+    tr = oracle.bfs_trace(g, depth, levels)
+    assert levels == len(ex["expected_directions_beamer"])
+    for key, want in ex["expected_trace"].items():
+        assert tr[key].tolist() == want, key
+    got = oracle.direction_schedule(tr, n, ex["alpha"], ex["beta"], heuristic="beamer")
+    assert got == ex["expected_directions_beamer"]
+    assert oracle.direction_schedule(tr, n, ex["alpha"], ex["beta"], heuristic="ratio") == \
+        ex["expected_directions_ratio"]
+
+
+@pytest.mark.parametrize("n", [10, 17, 40])
+def test_direction_rule_beamer_path_closed_form(n):
+    """Path 0 - 1 - ... - n-1 from vertex 0: after step k the new frontier {k+1} has
+    2 out-edges (1 for the last vertex) and the unvisited vertices {k+2 .. n-1}
+    have 2(n-k-2) - 1 in-edges, so with alpha = 1/4 the first switch to pull
+    follows step k = n - 6 (2/7 > 1/4 >= 2/9); each pull level finds one vertex,
+    1/n < beta = 1/8 sends it back to push, and the last step stays in push
+    because nothing is left unvisited (m_u = 0)."""
+    g = oracle.graph(*synth.path_edges(n))
+    depth, _, levels = oracle.bfs(g, 0)
+    tr = oracle.bfs_trace(g, depth, levels)
+    assert levels == n
+    want = ["push"] * (n - 5) + ["pull", "push", "pull", "push", "push"]
+    assert oracle.direction_schedule(tr, n, 0.25, 0.125, heuristic="beamer") == want
+
+
 def test_direction_rule_mesh_stays_push():
     """Section 6.3: the mesh-like graphs' best schedule is push-only; with
     alpha = 0.01 a grid frontier (<= ~2*sqrt(n)) stays below it once n > 4e4."""
