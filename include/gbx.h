@@ -265,11 +265,18 @@ gbx_status gbx_mxv_stats(const gbx_graph* A, int64_t* rows, int64_t* examined, i
  * (8 MiB) stays allocated on every GPU that loads the library until exit.  No
  * cudaMalloc, cudaFree or allocating library routine is called.  The first call
  * on a device looks up the array's device address (cudaGetSymbolAddress with
- * that device current); make that first call before any stream capture.  All
+ * that device current).  With CUDA's default lazy module loading that first
+ * call is also when the library's module, and the 8 MiB array with it, is
+ * placed on the device: it can allocate device memory, synchronise, and fail
+ * with GBX_ERR_OUT_OF_MEMORY.  So make one warm-up call per device at start-up,
+ * before any stream capture; later calls allocate nothing.  The address is kept
+ * for the life of the process: do not call this entry point again after
+ * cudaDeviceReset on a device it has used.  All
  * calls share the array: calls whose work overlaps on the GPU (different
  * streams, or concurrent host threads) race and must be ordered by the caller.
  * Each call rewrites every scratch word it reads.  Asynchronous on `stream`.
- * Errors: INVALID_VALUE, NULL_POINTER, NOT_SUPPORTED (device index >= 64), CUDA.
+ * Errors: INVALID_VALUE, NULL_POINTER, NOT_SUPPORTED (device index >= 64),
+ * OUT_OF_MEMORY (first call: the array could not be placed), CUDA.
  */
 gbx_status gbx_mxv_pull_noalloc(int32_t n, const int32_t* row_ptr, const int32_t* col, const uint8_t* u,
                                 const uint8_t* mask, int32_t mask_complement, int32_t early_exit, uint8_t* w,

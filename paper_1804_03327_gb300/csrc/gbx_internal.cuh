@@ -307,6 +307,23 @@ inline gbx_status check_graph(const gbx_graph* g) {
 inline Graph* as_impl(gbx_graph* g) { return reinterpret_cast<Graph*>(g); }
 inline const Graph* as_impl(const gbx_graph* g) { return reinterpret_cast<const Graph*>(g); }
 
+// The row-based masked matvec of gbx_mxv (mxv.cu), also launched by the
+// allocation-free entry point (noalloc.cu).  It must be launched with
+// kMxvThreads threads per block: its shared tile is sized from that constant.
+constexpr int kMxvThreads = 256;
+
+// Per-call counters of gbx_mxv (desc.trace): [0] rows computed by pull, [1]
+// entries examined by pull, [2] nonzeros of u expanded by push, [3] edges expanded.
+struct MxvStats {
+    unsigned long long rows, exam, ucount, edges, pad[4];
+};
+
+__global__ void __launch_bounds__(kMxvThreads)
+    mxv_pull_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col, const int32_t* __restrict__ first,
+                    const uint32_t* __restrict__ nzrows, const uint32_t* __restrict__ ubm,
+                    const uint32_t* __restrict__ pass, uint32_t* __restrict__ R, int32_t nwords, int early_exit,
+                    const int32_t* flag, MxvStats* stats, int32_t* huge, int32_t* huge_next, int32_t* huge_count);
+
 // Batched BFS internals (msbfs.cu), shared with the server.
 gbx_status ms_reserve(Workspace& w, int32_t n, int32_t S, cudaStream_t s);
 int64_t ms_scratch_bytes(int32_t n, int32_t S);

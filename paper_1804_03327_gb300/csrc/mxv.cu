@@ -19,17 +19,10 @@
 
 namespace gbx {
 
-constexpr int kMxvThreads = 256;
 constexpr int kMxvProbe = 16;
 constexpr int kMxvLaneRow = 32;
 constexpr int kMxvHugeRow = 4096;  // rows longer than this are spread over every warp
 constexpr int kMxvChunk = 1024;
-
-// Per-call counters (desc.trace): [0] rows computed by pull, [1] entries
-// examined by pull, [2] nonzeros of u expanded by push, [3] edges expanded.
-struct MxvStats {
-    unsigned long long rows, exam, ucount, edges, pad[4];
-};
 
 __device__ __forceinline__ bool dir_enabled(const int32_t* flag, int want) { return !flag || *flag == want; }
 

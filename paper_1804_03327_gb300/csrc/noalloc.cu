@@ -26,13 +26,6 @@ static std::mutex g_noalloc_mu;
 static uint32_t* g_noalloc_addr[kNoAllocMaxDevices] = {};
 static int g_noalloc_sms[kNoAllocMaxDevices] = {};
 
-// The row-based masked matvec kernel of gbx_mxv (mxv.cu).
-struct MxvStats;
-__global__ void mxv_pull_kernel(const int32_t* ptr, const int32_t* col, const int32_t* first, const uint32_t* nzrows,
-                                const uint32_t* ubm, const uint32_t* pass, uint32_t* R, int32_t nwords, int early_exit,
-                                const int32_t* flag, MxvStats* stats, int32_t* huge, int32_t* huge_next,
-                                int32_t* huge_count);
-
 __global__ void noalloc_nonempty_rows_kernel(const int32_t* __restrict__ row_ptr, int32_t n, uint32_t* __restrict__ bm) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nw32 = ((int64_t)n + 31) & ~(int64_t)31;
@@ -44,7 +37,10 @@ __global__ void noalloc_nonempty_rows_kernel(const int32_t* __restrict__ row_ptr
 
 // Device address of the scratch array on the current device.  The first call on a
 // device looks it up (cudaGetSymbolAddress, with that device current) and caches
-// it; host code never hands the array's host-side name to a kernel.
+// it; host code never hands the array's host-side name to a kernel.  The cached
+// address belongs to the device's context of that moment: after cudaDeviceReset
+// the module may be loaded elsewhere, so this entry point must not be called
+// again in a process that reset a device it used.
 static gbx_status noalloc_scratch(uint32_t** out, int* sms) {
     int dev = 0;
     GBX_CUDA_TRY(cudaGetDevice(&dev));
@@ -52,8 +48,16 @@ static gbx_status noalloc_scratch(uint32_t** out, int* sms) {
               "gbx_mxv_pull_noalloc supports device indices below 64");
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
     if (!g_noalloc_addr[dev]) {
+        // With lazy module loading (CUDA's default) this is where the library's module,
+        // and with it the array, is put on the device: it can allocate and fail.
         void* p = nullptr;
-        GBX_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            set_error(std::string("gbx_mxv_pull_noalloc: could not place its fixed scratch array on device ") +
+                      std::to_string(dev) + " (" + cudaGetErrorString(e) + ")");
+            return e == cudaErrorMemoryAllocation ? GBX_ERR_OUT_OF_MEMORY : GBX_ERR_CUDA;
+        }
         int nsm = 0;
         GBX_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
         g_noalloc_addr[dev] = static_cast<uint32_t*>(p);
@@ -96,7 +100,7 @@ extern "C" gbx_status gbx_mxv_pull_noalloc(int32_t n, const int32_t* row_ptr, co
         if (mask) GBX_TRY(pack_dense_to_bitmap(mask, n, mask_complement ? 1u : 0u, pass, s));
         const int64_t nw32 = ((int64_t)n + 31) & ~(int64_t)31;
         noalloc_nonempty_rows_kernel<<<div_up(nw32, 256), 256, 0, s>>>(row_ptr, n, nzrows);
-        mxv_pull_kernel<<<sms * 8, 256, 0, s>>>(row_ptr, col, nullptr, nzrows, ubm, mask ? pass : nullptr, R, nwords,
+        mxv_pull_kernel<<<sms * 8, kMxvThreads, 0, s>>>(row_ptr, col, nullptr, nzrows, ubm, mask ? pass : nullptr, R, nwords,
                                                 early_exit ? 1 : 0, nullptr, nullptr, nullptr, nullptr, nullptr);
     }
     GBX_TRY(bitmap_to_dense(R, n, nullptr, w, s));

@@ -303,6 +303,27 @@ def test_full_size_rmat22_all_workload_sources():
         for v in pick[:200]:
             p = parent[v]
             assert v in og.out_col[og.out_ptr[p]:og.out_ptr[p + 1]]
+    # the level trace behind the benchmark's byte model, at full size: every field of
+    # four sources' traced runs with the tuned descriptor against the oracle's trace,
+    # and the schedule against the oracle's rule with the tuned thresholds
+    traced = [srcs[k] for k in (0, 16, 32, 48)]
+    with ThreadPoolExecutor(4) as ex:
+        otrs = list(ex.map(lambda x: oracle.bfs_trace(og, wants[srcs.index(x)], int(wants[srcs.index(x)].max()) + 1),
+                           traced))
+    dtrace = gbx.Desc.from_buffer_copy(tuned)
+    dtrace.trace = 1
+    heur = "ratio" if tuned.heuristic == gbx.HEUR_RATIO else "beamer"
+    for src, otr in zip(traced, otrs):
+        depth, _ = run_bfs(g, n, src, dtrace)
+        assert np.array_equal(depth, wants[srcs.index(src)])
+        tr = gbx.bfs_trace(g)
+        assert len(tr) == len(otr)
+        for f in ["nf", "mf", "nu", "nu_nz", "mu", "n_new", "mf_new"]:
+            assert np.array_equal(tr[f], otr[f]), (src, f)
+        pull = tr["direction"] == gbx.DIR_PULL
+        assert np.array_equal(tr["e_exam"][pull], otr["e_exam"][pull]), src
+        got_dirs = ["push" if x == gbx.DIR_PUSH else "pull" for x in tr["direction"]]
+        assert got_dirs == oracle.direction_schedule(otr, n, tuned.alpha, tuned.beta, heuristic=heur), src
     g.free()
 
 
