@@ -68,24 +68,18 @@ struct BfsArgs {
     unsigned int bar_parity;
 };
 
-__device__ __forceinline__ void flush_acc(const Acc& acc, LevelCtr* cout, bool with_exam) {
-    const unsigned long long a = warp_sum_u64(acc.n_new);
-    const unsigned long long b = warp_sum_u64(acc.mf);
-    const unsigned long long c = warp_sum_u64(acc.indeg);
-    const unsigned long long d = with_exam ? warp_sum_u64(acc.exam) : 0ull;
-    if ((threadIdx.x & 31) == 0) {
-        if (a) atomicAdd(&cout->n_new, a);
-        if (b) atomicAdd(&cout->mf_new, b);
-        if (c) atomicAdd(&cout->indeg_new, c);
-        if (d) atomicAdd(&cout->e_exam, d);
-    }
+// Adds the block's counts of this level to cout (every thread of the block calls it).
+__device__ __forceinline__ void flush_acc(const Acc& acc, LevelCtr* cout, bool with_exam,
+                                          unsigned long long (*sm)[4]) {
+    block_add_counts<kBfsThreads / 32>(sm, acc.n_new, acc.mf, acc.indeg, with_exam ? acc.exam : 0ull, &cout->n_new,
+                                       &cout->mf_new, &cout->indeg_new, &cout->e_exam);
 }
 
 // ---------------------------------------------------------------- push (Eq 5)
 
 
 __device__ __forceinline__ void push_level(const BfsArgs& a, int32_t L, int cur, int vcur, uint32_t qcount,
-                                           uint32_t qedges, Stage& stg, Acc& acc) {
+                                           uint32_t qedges, Stage& stg, unsigned long long* bsm, Acc& acc) {
     const int gwarp = (int)((blockIdx.x * kBfsThreads + threadIdx.x) >> 5);
     const int nwarps = (int)((gridDim.x * kBfsThreads) >> 5);
     const int32_t* q = a.q[cur];
@@ -137,7 +131,7 @@ __device__ __forceinline__ void push_level(const BfsArgs& a, int32_t L, int cur,
             now = nxt;
         }
     }
-    stg.flush();
+    stg.flush_block<kBfsThreads / 32>(bsm);
 }
 
 // ---------------------------------------------------------------- pull (Eq 4, Algorithm 2)
@@ -227,7 +221,8 @@ __device__ __forceinline__ int warp_scan(const int32_t* __restrict__ in_col, con
 // finished by the whole warp, or by the whole grid when they are very long.
 template <bool kHuge>
 __device__ __forceinline__ void pull_level(const BfsArgs& a, int32_t L, int vcur, bool use_fbm, bool append,
-                                           const HugeRows& hr, Stage& st, uint32_t* snew, Acc& acc) {
+                                           const HugeRows& hr, Stage& st, unsigned long long* bsm, uint32_t* snew,
+                                           Acc& acc) {
     const int lane = threadIdx.x & 31;
     const int gwarp = (int)((blockIdx.x * kBfsThreads + threadIdx.x) >> 5);
     const int nwarps = (int)((gridDim.x * kBfsThreads) >> 5);
@@ -416,7 +411,7 @@ __device__ __forceinline__ void pull_level(const BfsArgs& a, int32_t L, int vcur
         if (wok) vnext[w] = cw | snew[lane];
         __syncwarp();
     }
-    if (append) st.flush();
+    if (append) st.flush_block<kBfsThreads / 32>(bsm);
 }
 
 // The grid-wide phase of a pull level: warps take the listed long rows' edge
@@ -431,7 +426,7 @@ __device__ __forceinline__ void pull_level(const BfsArgs& a, int32_t L, int vcur
 #endif
 __device__ GBX_PULL_HUGE_INLINE void pull_huge(const BfsArgs& a, int32_t L, int cur, int vcur, int32_t entries,
                                                int32_t chunks, bool exact_exam, StageBuf* sb, LevelCtr* cout,
-                                               Acc& acc) {
+                                               unsigned long long* bsm, Acc& acc) {
     const int lane = threadIdx.x & 31;
     // everything below is rebuilt from the arguments so that little stays live across the level
     const bool use_fbm = !a.operand_reuse;
@@ -497,7 +492,7 @@ __device__ GBX_PULL_HUGE_INLINE void pull_huge(const BfsArgs& a, int32_t L, int 
         }
         if (append) st.put(isnew && od > 0, i);
     }
-    if (append) st.flush();
+    if (append) st.flush_block<kBfsThreads / 32>(bsm);
 }
 
 // Edges a row-ordered scan with early exit examines in the listed rows: up to
@@ -514,7 +509,7 @@ __device__ __forceinline__ void pull_huge_exam(const BfsArgs& a, const HugeRows&
 }
 
 // DENSE2SPARSE at a pull -> push switch: F_{L+1} = visited now AND NOT visited before.
-__device__ __forceinline__ void bitmap_to_queue(const BfsArgs& a, int vcur, Stage& st) {
+__device__ __forceinline__ void bitmap_to_queue(const BfsArgs& a, int vcur, Stage& st, unsigned long long* bsm) {
     const int lane = threadIdx.x & 31;
     const int gwarp = (int)((blockIdx.x * kBfsThreads + threadIdx.x) >> 5);
     const int nwarps = (int)((gridDim.x * kBfsThreads) >> 5);
@@ -531,7 +526,7 @@ __device__ __forceinline__ void bitmap_to_queue(const BfsArgs& a, int vcur, Stag
             st.put((nw >> lane) & 1u, (((tile << 5) + j) << 5) + lane);
         }
     }
-    st.flush();
+    st.flush_block<kBfsThreads / 32>(bsm);
 }
 
 // out[i] = fill for all i < n except out[special] = special_value; 16-byte stores when aligned.
@@ -601,6 +596,8 @@ __global__ void __launch_bounds__(kBfsThreads, kBfsMinBlocks) bfs_kernel(BfsArgs
     __shared__ StageBuf stage_mem[kBfsThreads / 32];
     __shared__ uint32_t tile_new[kBfsThreads / 32][32];
     __shared__ unsigned long long lvl[6];  // counters of the level just finished, read once per block
+    __shared__ unsigned long long acc_mem[kBfsThreads / 32][4];  // per-warp counts before the block's atomics
+    __shared__ unsigned long long stage_sum[kBfsThreads / 32];   // per-warp queue ranges of a block flush
     const int wib = threadIdx.x >> 5;
     unsigned long long qv = s_od > 0 ? (((unsigned long long)s_od << 32) | 1ull) : 0ull;
     int dir = a.mode == GBX_DIR_PULL ? DIR_PULL : DIR_PUSH;
@@ -618,7 +615,7 @@ __global__ void __launch_bounds__(kBfsThreads, kBfsMinBlocks) bfs_kernel(BfsArgs
         Stage st{stage_mem + wib, 0, cout, a.q[cur ^ 1], a.qp[cur ^ 1], a.qd[cur ^ 1],
                  a.out_ptr, a.in_ptr, dir == DIR_PUSH, a.need_indeg, &acc};
         if (dir == DIR_PUSH) {
-            push_level(a, L, cur, vcur, qcount, qedges, st, acc);
+            push_level(a, L, cur, vcur, qcount, qedges, st, stage_sum, acc);
             appended = true;
         } else {
             const bool use_fbm = !a.operand_reuse;
@@ -634,9 +631,9 @@ __global__ void __launch_bounds__(kBfsThreads, kBfsMinBlocks) bfs_kernel(BfsArgs
             }
             appended = use_fbm;
             pull_level<kHuge>(a, L, vcur, use_fbm, appended, HugeRows{a.q[cur], a.qp[cur], a.qd[cur], a.hfirst}, st,
-                       tile_new[wib], acc);
+                              stage_sum, tile_new[wib], acc);
         }
-        flush_acc(acc, cout, kTrace);
+        flush_acc(acc, cout, kTrace, acc_mem);
         if (!grid_barrier(barc, gridDim.x, bar_round, a.status, a.timeout_ns)) return;
         if (threadIdx.x == 0) {
             lvl[0] = ld_volatile_u64(&cout->n_new);
@@ -650,13 +647,14 @@ __global__ void __launch_bounds__(kBfsThreads, kBfsMinBlocks) bfs_kernel(BfsArgs
         if (kHuge && lvl[5] != 0ull) {  // the pull level listed long rows: the grid scans them now
             const int32_t entries = (int32_t)(uint32_t)lvl[5];
             Acc acc2;
-            pull_huge(a, L, cur, vcur, entries, (int32_t)(lvl[5] >> 32), kTrace, stage_mem + wib, cout, acc2);
-            flush_acc(acc2, cout, kTrace);
+            pull_huge(a, L, cur, vcur, entries, (int32_t)(lvl[5] >> 32), kTrace, stage_mem + wib, cout, stage_sum,
+                      acc2);
+            flush_acc(acc2, cout, kTrace, acc_mem);
             if (!grid_barrier(barc, gridDim.x, bar_round, a.status, a.timeout_ns)) return;
             if (kTrace && a.early_exit) {
                 Acc acc3;
                 pull_huge_exam(a, HugeRows{a.q[cur], a.qp[cur], a.qd[cur], a.hfirst}, entries, acc3);
-                flush_acc(acc3, cout, true);
+                flush_acc(acc3, cout, true, acc_mem);
                 if (!grid_barrier(barc, gridDim.x, bar_round, a.status, a.timeout_ns)) return;
             }
             if (threadIdx.x == 0) {
@@ -713,7 +711,7 @@ __global__ void __launch_bounds__(kBfsThreads, kBfsMinBlocks) bfs_kernel(BfsArgs
         }
         if (dir == DIR_PULL) vcur ^= 1;
         if (dir == DIR_PULL && next == DIR_PUSH && !appended) {
-            bitmap_to_queue(a, vcur, st);
+            bitmap_to_queue(a, vcur, st, stage_sum);
             if (!grid_barrier(barc, gridDim.x, bar_round, a.status, a.timeout_ns)) return;
             if (threadIdx.x == 0) lvl[4] = ld_volatile_u64(&cout->q);
             __syncthreads();

@@ -104,6 +104,84 @@ struct Stage {
         __syncwarp();
     }
 
+    // End-of-level publish by the whole block (every thread of the block calls it):
+    // the warps' staged vertices go out with one packed atomic for the block instead
+    // of one per warp, the warps' ranges placed by a scan over the block in bsm
+    // (kWarps shared words that no other code touches until the next block barrier).
+    template <int kWarps>
+    __device__ __forceinline__ void flush_block(unsigned long long* bsm) {
+        __syncwarp();
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        constexpr int R = kStage / 32;
+        int32_t v[R], rs[R], od[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            const int idx = t * 32 + lane;
+            v[t] = idx < cnt ? sb->v[idx] : -1;
+        }
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            rs[t] = v[t] >= 0 ? __ldg(out_ptr + v[t]) : 0;
+            od[t] = v[t] >= 0 ? __ldg(out_ptr + v[t] + 1) - rs[t] : 0;
+        }
+        if (count_degrees) {
+#pragma unroll
+            for (int t = 0; t < R; ++t) {
+                acc->mf += (unsigned long long)od[t];
+                if (need_indeg)
+                    acc->indeg += v[t] >= 0 ? (unsigned long long)(__ldg(in_ptr + v[t] + 1) - __ldg(in_ptr + v[t])) : 0ull;
+                else
+                    acc->indeg += (unsigned long long)od[t];
+            }
+        }
+        uint32_t keep[R];
+        uint32_t nkeep = 0, sum = 0;
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            keep[t] = __ballot_sync(0xffffffffu, od[t] > 0);
+            nkeep += __popc(keep[t]);
+            sum += (uint32_t)od[t];
+        }
+        const uint32_t tot = __reduce_add_sync(0xffffffffu, sum);
+        if (lane == 0) bsm[w] = ((unsigned long long)tot << 32) | (unsigned long long)nkeep;
+        __syncthreads();
+        if (w == 0) {
+            // packed (degree sum, count) pairs add without carries: both halves stay below 2^32
+            const unsigned long long own = lane < kWarps ? bsm[lane] : 0ull;
+            unsigned long long x = own;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            const unsigned long long total = __shfl_sync(0xffffffffu, x, 31);
+            unsigned long long old = 0;
+            if (lane == 0 && total) old = atomicAdd(&cout->q, total);
+            old = __shfl_sync(0xffffffffu, old, 0);
+            __syncwarp();
+            if (lane < kWarps) bsm[lane] = old + x - own;
+        }
+        __syncthreads();
+        const unsigned long long base = bsm[w];
+        int32_t pos = (int32_t)(uint32_t)base;
+        uint32_t pre_base = (uint32_t)(base >> 32);
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            const uint32_t inc = warp_inclusive_sum((uint32_t)od[t]);
+            if (od[t] > 0) {
+                const int32_t p = pos + __popc(keep[t] & lanemask_lt());
+                const int32_t pre = (int32_t)(pre_base + inc - (uint32_t)od[t]);
+                nq[p] = v[t];
+                nqp[p] = pre;
+                nqd[p] = rs[t] - pre;
+            }
+            pos += __popc(keep[t]);
+            pre_base += __shfl_sync(0xffffffffu, inc, 31);
+        }
+        cnt = 0;
+        __syncwarp();
+    }
+
     // Stage the lanes with `take` (all 32 lanes call this).
     __device__ __forceinline__ void put(bool take, int32_t v) {
         const uint32_t app = __ballot_sync(0xffffffffu, take);
@@ -114,6 +192,44 @@ struct Stage {
         __syncwarp();
     }
 };
+
+// A level's counters, added once per block.  Each warp leaves its sums in shared
+// memory; after a block barrier warp 0 adds them up and thread 0 adds the block's
+// totals to the global counters, one atomic per counter and block.  The counters
+// of a level share one cache line, and same-line atomics serialise at one L2 slice,
+// so one atomic per warp from a grid of thousands of warps costs microseconds per
+// level.  Every thread of the block calls this; a null counter is skipped.  Thread
+// 0 issues the atomics, so its arrival at the next grid barrier (a release) orders
+// them before the barrier completes.
+template <int kWarps>
+__device__ __forceinline__ void block_add_counts(unsigned long long (*sm)[4], unsigned long long x0,
+                                                 unsigned long long x1, unsigned long long x2, unsigned long long x3,
+                                                 unsigned long long* c0, unsigned long long* c1,
+                                                 unsigned long long* c2, unsigned long long* c3) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    x0 = warp_sum_u64(x0);
+    x1 = warp_sum_u64(x1);
+    x2 = warp_sum_u64(x2);
+    x3 = warp_sum_u64(x3);
+    if (lane == 0) {
+        sm[w][0] = x0;
+        sm[w][1] = x1;
+        sm[w][2] = x2;
+        sm[w][3] = x3;
+    }
+    __syncthreads();
+    if (w == 0) {
+        unsigned long long y[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) y[k] = warp_sum_u64(lane < kWarps ? sm[lane][k] : 0ull);
+        if (lane == 0) {
+            if (c0 && y[0]) atomicAdd(c0, y[0]);
+            if (c1 && y[1]) atomicAdd(c1, y[1]);
+            if (c2 && y[2]) atomicAdd(c2, y[2]);
+            if (c3 && y[3]) atomicAdd(c3, y[3]);
+        }
+    }
+}
 
 // Largest k in [0, count) with qp[k] <= e (qp ascending, qp[0] = 0), found by the
 // whole warp: 32 samples per round shrink the range 32-fold.
@@ -150,8 +266,12 @@ struct PushCursor {
     int32_t wlast;
     int32_t wv[kPushIlp];
 
-    __device__ __forceinline__ PushStep gather(const int32_t* out_col, const int32_t* q, const int32_t* qp,
-                                               const int32_t* qd, uint32_t qcount, int32_t base, int32_t e1) {
+    // Maps the edges [base, base + kPushStep) of one step (lane t-th slot: edge
+    // base + 32 t + lane) to their queue entries and loads each edge's frontier
+    // vertex u (-1 at or past e1) and d = (row start - prefix) of its entry, so that
+    // the edge's CSR position is e + d.  The loads are issued, not waited for.
+    __device__ __forceinline__ void map(const int32_t* q, const int32_t* qp, const int32_t* qd, uint32_t qcount,
+                                        int32_t base, int32_t e1, int32_t (&u)[kPushIlp], int32_t (&d)[kPushIlp]) {
         const int lane = threadIdx.x & 31;
         if (wlast <= base + kPushStep - 1) {
 #pragma unroll
@@ -173,23 +293,34 @@ struct PushCursor {
             }
             occ[m] = __reduce_or_sync(0xffffffffu, c);
         }
-        PushStep st;
         uint32_t before = 0;
 #pragma unroll
         for (int t = 0; t < kPushIlp; ++t) {
             const int32_t kk = k + (int32_t)(before + __popc(occ[t] & (0xffffffffu >> (31 - lane))));
             before += __popc(occ[t]);
             const int32_t e = base + 32 * t + lane;
-            st.u[t] = -1;
-            st.v[t] = 0;
-            st.k[t] = 0;
+            u[t] = -1;
+            d[t] = 0;
             if (e < e1) {
-                st.u[t] = q[kk];
-                st.k[t] = e + qd[kk];
-                st.v[t] = __ldg(out_col + st.k[t]);
+                u[t] = q[kk];
+                d[t] = qd[kk];
             }
         }
         k += (int32_t)before;
+    }
+
+    __device__ __forceinline__ PushStep gather(const int32_t* out_col, const int32_t* q, const int32_t* qp,
+                                               const int32_t* qd, uint32_t qcount, int32_t base, int32_t e1) {
+        const int lane = threadIdx.x & 31;
+        int32_t u[kPushIlp], d[kPushIlp];
+        map(q, qp, qd, qcount, base, e1, u, d);
+        PushStep st;
+#pragma unroll
+        for (int t = 0; t < kPushIlp; ++t) {
+            st.u[t] = u[t];
+            st.k[t] = u[t] >= 0 ? base + 32 * t + lane + d[t] : 0;
+            st.v[t] = u[t] >= 0 ? __ldg(out_col + st.k[t]) : 0;
+        }
         return st;
     }
 };

@@ -403,6 +403,7 @@ __global__ void __launch_bounds__(kMsThreads, kOcc) ms_bfs_kernel(MsArgs a) {
     const long long gstride = (long long)gridDim.x * kMsThreads;
     __shared__ StageBuf stage_mem[kMsThreads / 32];
     __shared__ unsigned long long lvl[6];
+    __shared__ unsigned long long acc_mem[kMsThreads / 32][4];
     const int wib = threadIdx.x >> 5;
     unsigned int* barc = a.bar->count + a.bar_parity;
     unsigned int bar_round = 0;
@@ -514,16 +515,8 @@ __global__ void __launch_bounds__(kMsThreads, kOcc) ms_bfs_kernel(MsArgs a) {
         } else {
             ms_pull<CW>(a, L, a.Fb[r1], st, acc);
         }
-        {
-            const unsigned long long x = warp_sum_u64(acc.n_new);
-            const unsigned long long y = warp_sum_u64(acc.mf);
-            const unsigned long long z = warp_sum_u64(acc.exam);
-            if ((threadIdx.x & 31) == 0) {
-                if (x) atomicAdd(&cout->n_new, x);
-                if (y) atomicAdd(&cout->mf_new, y);
-                if (z) atomicAdd(&cout->e_exam, z);
-            }
-        }
+        block_add_counts<kMsThreads / 32>(acc_mem, acc.n_new, acc.mf, acc.exam, 0ull, &cout->n_new, &cout->mf_new,
+                                          &cout->e_exam, nullptr);
         if (!grid_barrier(barc, gridDim.x, bar_round, a.status, a.timeout_ns)) return;
         if (threadIdx.x == 0) {
             lvl[0] = ld_volatile_u64(&cout->n_new);

@@ -190,6 +190,7 @@ __global__ void __launch_bounds__(kSsspThreads, kOcc) sssp_kernel(SsspArgs a) {
 
     __shared__ StageBuf stage_mem[kSsspThreads / 32];
     __shared__ unsigned long long lvl[4];
+    __shared__ unsigned long long acc_mem[kSsspThreads / 32][4];
     const int wib = threadIdx.x >> 5;
     unsigned long long qv = s_od > 0 ? (((unsigned long long)s_od << 32) | 1ull) : 0ull;
     int dir = a.mode == GBX_DIR_PULL ? GBX_DIR_PULL : GBX_DIR_PUSH;
@@ -210,16 +211,8 @@ __global__ void __launch_bounds__(kSsspThreads, kOcc) sssp_kernel(SsspArgs a) {
         else
             sssp_pull(a, acc);
         // counts: n_new, mf_new (push: from the staged degrees), examined edges
-        {
-            const unsigned long long x0 = warp_sum_u64(acc.n_new);
-            const unsigned long long x1 = warp_sum_u64(acc.mf);
-            const unsigned long long x3 = warp_sum_u64(acc.exam);
-            if ((threadIdx.x & 31) == 0) {
-                if (x0) atomicAdd(&cout->n_new, x0);
-                if (x1) atomicAdd(&cout->mf_new, x1);
-                if (x3) atomicAdd(&cout->e_exam, x3);
-            }
-        }
+        block_add_counts<kSsspThreads / 32>(acc_mem, acc.n_new, acc.mf, acc.exam, 0ull, &cout->n_new, &cout->mf_new,
+                                            &cout->e_exam, nullptr);
         if (!grid_barrier(barc, gridDim.x, bar_round, a.status, a.timeout_ns)) return;
         if (threadIdx.x == 0) {
             lvl[0] = ld_volatile_u64(&cout->n_new);
