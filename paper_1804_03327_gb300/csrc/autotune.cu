@@ -83,9 +83,10 @@ extern "C" gbx_status gbx_autotune(gbx_graph* g, int32_t kind, const int32_t* so
     gbx_desc base;
     gbx_desc_init(&base);
     if (kind == GBX_TUNE_BFS) {
-        const float ratio_a[] = {0.002f, 0.005f, 0.01f, 0.02f, 0.05f, 0.1f};
-        const float beamer_a[] = {1.0f / 64, 1.0f / 32, 1.0f / 16, 1.0f / 14, 1.0f / 8, 1.0f / 4};
-        const float betas[] = {0.01f, 0.05f};
+        const float ratio_a[] = {0.0005f, 0.001f, 0.002f, 0.005f, 0.01f, 0.02f, 0.05f, 0.1f};
+        const float beamer_a[] = {1.0f / 256, 1.0f / 128, 1.0f / 64, 1.0f / 32, 1.0f / 16, 1.0f / 14, 1.0f / 8, 1.0f / 4};
+        // beta = 0: once pulling, never back to push (the tail levels stay row-based)
+        const float betas[] = {0.0f, 0.001f, 0.01f, 0.05f};
         for (float b : betas) {
             for (float a : ratio_a) {
                 gbx_desc d = base;

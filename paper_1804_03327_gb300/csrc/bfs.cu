@@ -78,8 +78,21 @@ __device__ __forceinline__ void flush_acc(const Acc& acc, LevelCtr* cout, bool w
 // ---------------------------------------------------------------- push (Eq 5)
 
 
+// The warp's edge range is walked as a software pipeline of four stages, each on
+// a different step of kBfsStep edges: (1) map the edges to queue entries and load
+// their frontier vertex and row offset, (2) load the child, (3) load the child's
+// visited word, (4) claim unvisited children with atomicOr.  One iteration issues
+// the memory operations of all four stages (on steps s, s-1, s-2, s-3) before it
+// waits for any of them, so a step costs about one memory round trip instead of
+// four dependent ones.
+#ifndef GBX_BFS_PUSH_ILP
+#define GBX_BFS_PUSH_ILP 1
+#endif
+constexpr int kBfsIlp = GBX_BFS_PUSH_ILP;  // edges per lane and step (2 needs more than the 64 registers)
+constexpr int kBfsStep = 32 * kBfsIlp;
 __device__ __forceinline__ void push_level(const BfsArgs& a, int32_t L, int cur, int vcur, uint32_t qcount,
                                            uint32_t qedges, Stage& stg, unsigned long long* bsm, Acc& acc) {
+    const int lane = threadIdx.x & 31;
     const int gwarp = (int)((blockIdx.x * kBfsThreads + threadIdx.x) >> 5);
     const int nwarps = (int)((gridDim.x * kBfsThreads) >> 5);
     const int32_t* q = a.q[cur];
@@ -88,47 +101,95 @@ __device__ __forceinline__ void push_level(const BfsArgs& a, int32_t L, int cur,
     uint32_t* vis = a.vis[vcur];
     const int32_t E = (int32_t)qedges;
     int32_t chunk = (int32_t)(((long long)E + nwarps - 1) / nwarps);
-    chunk = chunk < kPushStep ? kPushStep : ((chunk + kPushStep - 1) / kPushStep) * kPushStep;
+    chunk = chunk < kBfsStep ? kBfsStep : ((chunk + kBfsStep - 1) / kBfsStep) * kBfsStep;
     for (long long e0l = (long long)gwarp * chunk; e0l < E; e0l += (long long)nwarps * chunk) {
         const int32_t e0 = (int32_t)e0l;
         const int32_t e1 = E - e0 > chunk ? e0 + chunk : E;
-        PushCursor cur_;
+        const int32_t nsteps = (e1 - e0 + kBfsStep - 1) / kBfsStep;
+        PushCursorT<kBfsIlp> cur_;
         cur_.k = warp_find_entry(qp, (int32_t)qcount, e0);
         cur_.wlast = -1;
-        // two-stage pipeline: the children of step s + 1 are gathered (their loads in
-        // flight) while step s probes the visited bitmap and claims
-        PushStep now = cur_.gather(a.out_col, q, qp, qd, qcount, e0, e1);
-        for (int32_t base = e0; base < e1; base += kPushStep) {
-            PushStep nxt;
-            if (base + kPushStep < e1) {
-                nxt = cur_.gather(a.out_col, q, qp, qd, qcount, base + kPushStep, e1);
+        if (nsteps == 1) {
+            // a single step (a small frontier): no pipeline fill and drain
+            for (int32_t base = e0; base < e1; base += kBfsStep) {
+                const PushStepT<kBfsIlp> now = cur_.gather(a.out_col, q, qp, qd, qcount, base, e1);
+#pragma unroll
+                for (int t = 0; t < kBfsIlp; ++t) {
+                    const uint32_t bit = 1u << (now.v[t] & 31);
+                    const bool claimed = now.u[t] >= 0 && !(__ldca(vis + (now.v[t] >> 5)) & bit) &&
+                                         !(atomicOr(vis + (now.v[t] >> 5), bit) & bit);
+                    if (claimed) {
+                        a.depth[now.v[t]] = L + 1;
+                        if (a.parent) a.parent[now.v[t]] = now.u[t];
+                        acc.n_new += 1;
+                    }
+                    stg.put(claimed, now.v[t]);
+                }
+            }
+            continue;
+        }
+        // stage registers: u < 0 marks an empty slot (past e1, or pipeline fill and drain)
+        int32_t u1[kBfsIlp], d1[kBfsIlp];                 // after stage 1: vertex, row start - prefix
+        int32_t u2[kBfsIlp], v2[kBfsIlp];                 // after stage 2: vertex, child
+        int32_t u3[kBfsIlp], v3[kBfsIlp];                 // after stage 3: vertex, child, visited word
+        uint32_t w3[kBfsIlp];
+#pragma unroll
+        for (int t = 0; t < kBfsIlp; ++t) {
+            u1[t] = u2[t] = u3[t] = -1;
+            d1[t] = v2[t] = v3[t] = 0;
+            w3[t] = 0xffffffffu;
+        }
+        for (int32_t it = 0; it < nsteps + 3; ++it) {
+            // stage 4 (step it - 3): claim the children whose visited bit was clear
+            uint32_t old[kBfsIlp];
+#pragma unroll
+            for (int t = 0; t < kBfsIlp; ++t) {
+                const uint32_t bit = 1u << (v3[t] & 31);
+                // L1-cached probe of stage 3: a stale word only costs an extra atomic, the atomic decides
+                old[t] = (u3[t] >= 0 && !(w3[t] & bit)) ? atomicOr(vis + (v3[t] >> 5), bit) : 0xffffffffu;
+            }
+            // stage 3 (step it - 2): visited words of the children
+            uint32_t w2[kBfsIlp];
+#pragma unroll
+            for (int t = 0; t < kBfsIlp; ++t) w2[t] = u2[t] >= 0 ? __ldca(vis + (v2[t] >> 5)) : 0xffffffffu;
+            // stage 2 (step it - 1): children
+            int32_t c1[kBfsIlp];
+            const int32_t b1 = e0 + (it - 1) * kBfsStep;
+#pragma unroll
+            for (int t = 0; t < kBfsIlp; ++t) c1[t] = u1[t] >= 0 ? __ldg(a.out_col + b1 + 32 * t + lane + d1[t]) : 0;
+            // stage 1 (step it): queue entries
+            int32_t u0[kBfsIlp], d0[kBfsIlp];
+            if (it < nsteps) {
+                cur_.map(q, qp, qd, qcount, e0 + it * kBfsStep, e1, u0, d0);
             } else {
 #pragma unroll
-                for (int t = 0; t < kPushIlp; ++t) {
-                    nxt.u[t] = -1;
-                    nxt.v[t] = 0;
+                for (int t = 0; t < kBfsIlp; ++t) {
+                    u0[t] = -1;
+                    d0[t] = 0;
                 }
             }
-            uint32_t wd[kPushIlp];
+            // stage 4, continued: stamp the claimed children (the fused GrB_assign) and stage them
 #pragma unroll
-            for (int t = 0; t < kPushIlp; ++t) wd[t] = now.u[t] >= 0 ? __ldca(vis + (now.v[t] >> 5)) : 0xffffffffu;
-            bool claimed[kPushIlp];
-#pragma unroll
-            for (int t = 0; t < kPushIlp; ++t) {
-                const uint32_t bit = 1u << (now.v[t] & 31);
-                // L1-cached probe: a stale word only costs an extra atomic, the atomic decides
-                claimed[t] = !(wd[t] & bit) && !(atomicOr(vis + (now.v[t] >> 5), bit) & bit);
-            }
-#pragma unroll
-            for (int t = 0; t < kPushIlp; ++t) {
-                if (claimed[t]) {
-                    a.depth[now.v[t]] = L + 1;
-                    if (a.parent) a.parent[now.v[t]] = now.u[t];
+            for (int t = 0; t < kBfsIlp; ++t) {
+                const bool claimed = u3[t] >= 0 && !(old[t] & (1u << (v3[t] & 31)));
+                if (claimed) {
+                    a.depth[v3[t]] = L + 1;
+                    if (a.parent) a.parent[v3[t]] = u3[t];
                     acc.n_new += 1;
                 }
-                stg.put(claimed[t], now.v[t]);
+                stg.put(claimed, v3[t]);
             }
-            now = nxt;
+            // advance the pipeline
+#pragma unroll
+            for (int t = 0; t < kBfsIlp; ++t) {
+                u3[t] = u2[t];
+                v3[t] = v2[t];
+                w3[t] = w2[t];
+                u2[t] = u1[t];
+                v2[t] = c1[t];
+                u1[t] = u0[t];
+                d1[t] = d0[t];
+            }
         }
     }
     stg.flush_block<kBfsThreads / 32>(bsm);
@@ -553,6 +614,70 @@ __device__ __forceinline__ void fill_outputs(int32_t* out, int32_t n, int32_t fi
     }
 }
 
+struct LoopState {
+    unsigned long long qv;  // queue of the next level: entries (low 32 bits), out-degree sum (high 32)
+    long long nf, mf, mu;   // |F_L|, out-edges of F_L, in-edges of the rows unvisited before level L
+    unsigned long long t_mark;
+    int next, stop;
+};
+
+// End of level L, by thread 0 of every block (all blocks read the same counters and
+// decide alike): the trace record and the status words (block 0 only), the stop
+// test, and the direction of level L + 1 (Section 6.3).
+template <bool kTrace>
+__device__ __forceinline__ void level_end(const BfsArgs& a, int32_t L, int dir, const unsigned long long* lvl,
+                                          LoopState& ls) {
+    const long long n_new = (long long)lvl[0];
+    const long long mf_new = (long long)lvl[1];
+    const long long in_new = (long long)lvl[2];
+    const bool lead = blockIdx.x == 0;
+    if (kTrace && lead && L < a.trace_cap) {
+        LevelRec r;
+        r.direction = dir;
+        r.level = L;
+        r.nf = ls.nf;
+        r.mf = ls.mf;
+        r.mu = ls.mu;
+        r.e_exam = dir == DIR_PULL ? (long long)lvl[3] : -1;
+        r.n_new = n_new;
+        r.mf_new = mf_new;
+        const unsigned long long now = global_timer_ns();
+        r.t_ns = (long long)(now - ls.t_mark);
+        ls.t_mark = now;
+        a.trace[L] = r;
+    }
+    if (n_new == 0) {
+        if (lead) a.status[ST_LEVELS] = L + 1;
+        ls.stop = 1;
+        return;
+    }
+    if (L + 1 >= a.n) {  // a BFS has at most n levels; more means corrupted state
+        if (lead) atomicCAS(a.status + ST_ERROR, 0, (int)GBX_ERR_OVERFLOW);
+        ls.stop = 1;
+        return;
+    }
+    int next = dir;
+    if (a.mode == GBX_DIR_AUTO) {
+        const double r_new = (double)n_new / (double)a.n;
+        if (dir == DIR_PUSH) {
+            if (a.heuristic == GBX_HEUR_RATIO) {
+                if (r_new > (double)a.alpha && n_new > ls.nf) next = DIR_PULL;
+            } else {
+                const long long mu_next = ls.mu - in_new;
+                if (mu_next > 0 && (double)mf_new / (double)mu_next > (double)a.alpha) next = DIR_PULL;
+            }
+        } else if (r_new < (double)a.beta && (a.heuristic != GBX_HEUR_RATIO || n_new < ls.nf)) {
+            // the ratio rule also wants r decreasing; Beamer's way back is r < beta alone
+            next = DIR_PUSH;
+        }
+    }
+    ls.next = next;
+    ls.qv = lvl[4];
+    ls.mu -= in_new;
+    ls.nf = n_new;
+    ls.mf = mf_new;
+}
+
 // kHuge: long pull rows go to the grid-wide phase.  Launched for runs that
 // expect full row scans (no early exit, or pull on every level); with the
 // direction rule and early exit a pull level rarely meets a long row without a
@@ -598,17 +723,29 @@ __global__ void __launch_bounds__(kBfsThreads, kBfsMinBlocks) bfs_kernel(BfsArgs
     __shared__ unsigned long long lvl[6];  // counters of the level just finished, read once per block
     __shared__ unsigned long long acc_mem[kBfsThreads / 32][4];  // per-warp counts before the block's atomics
     __shared__ unsigned long long stage_sum[kBfsThreads / 32];   // per-warp queue ranges of a block flush
+    // block-uniform loop state, kept by thread 0 in shared memory rather than in every
+    // thread's registers (which the level code needs)
+    __shared__ LoopState ls;
     const int wib = threadIdx.x >> 5;
-    unsigned long long qv = s_od > 0 ? (((unsigned long long)s_od << 32) | 1ull) : 0ull;
+    if (threadIdx.x == 0) {
+        ls.qv = s_od > 0 ? (((unsigned long long)s_od << 32) | 1ull) : 0ull;
+        ls.nf = 1;
+        ls.mf = s_od;
+        ls.mu = a.nnz - s_id;
+        ls.t_mark = t_mark;
+        ls.next = 0;
+        ls.stop = 0;
+    }
+    __syncthreads();
     int dir = a.mode == GBX_DIR_PULL ? DIR_PULL : DIR_PUSH;
     int cur = 0, vcur = 0;
-    long long nf = 1, mf = s_od, mu = a.nnz - s_id;
     for (int32_t L = 0;; ++L) {
         LevelCtr* cout = a.ctr + ((L + 1) % 3);
         if (gtid == 0) {
             LevelCtr z = {};
             a.ctr[(L + 2) % 3] = z;
         }
+        const unsigned long long qv = ls.qv;
         const uint32_t qcount = (uint32_t)qv, qedges = (uint32_t)(qv >> 32);
         Acc acc;
         bool appended;
@@ -666,60 +803,17 @@ __global__ void __launch_bounds__(kBfsThreads, kBfsMinBlocks) bfs_kernel(BfsArgs
             }
             __syncthreads();
         }
-        const long long n_new = (long long)lvl[0];
-        const long long mf_new = (long long)lvl[1];
-        const long long in_new = (long long)lvl[2];
-        qv = lvl[4];
-        if (kTrace && gtid == 0 && L < a.trace_cap) {
-            LevelRec r;
-            r.direction = dir;
-            r.level = L;
-            r.nf = nf;
-            r.mf = mf;
-            r.mu = mu;
-            r.e_exam = dir == DIR_PULL ? (long long)lvl[3] : -1;
-            r.n_new = n_new;
-            r.mf_new = mf_new;
-            const unsigned long long now = global_timer_ns();
-            r.t_ns = (long long)(now - t_mark);
-            t_mark = now;
-            a.trace[L] = r;
-        }
-        if (n_new == 0) {
-            if (gtid == 0) a.status[ST_LEVELS] = L + 1;
-            return;
-        }
-        if (L + 1 >= a.n) {  // a BFS has at most n levels; more means corrupted state
-            if (gtid == 0) atomicCAS(a.status + ST_ERROR, 0, (int)GBX_ERR_OVERFLOW);
-            return;
-        }
-        // Section 6.3: choose the direction of level L + 1
-        int next = dir;
-        if (a.mode == GBX_DIR_AUTO) {
-            const double r_new = (double)n_new / (double)a.n;
-            if (dir == DIR_PUSH) {
-                if (a.heuristic == GBX_HEUR_RATIO) {
-                    if (r_new > (double)a.alpha && n_new > nf) next = DIR_PULL;
-                } else {
-                    const long long mu_next = mu - in_new;
-                    if (mu_next > 0 && (double)mf_new / (double)mu_next > (double)a.alpha) next = DIR_PULL;
-                }
-            } else if (r_new < (double)a.beta && (a.heuristic != GBX_HEUR_RATIO || n_new < nf)) {
-                // the ratio rule also wants r decreasing; Beamer's way back is r < beta alone
-                next = DIR_PUSH;
-            }
-        }
+        if (threadIdx.x == 0) level_end<kTrace>(a, L, dir, lvl, ls);
+        __syncthreads();
+        if (ls.stop) return;
+        const int next = ls.next;
         if (dir == DIR_PULL) vcur ^= 1;
         if (dir == DIR_PULL && next == DIR_PUSH && !appended) {
             bitmap_to_queue(a, vcur, st, stage_sum);
             if (!grid_barrier(barc, gridDim.x, bar_round, a.status, a.timeout_ns)) return;
-            if (threadIdx.x == 0) lvl[4] = ld_volatile_u64(&cout->q);
+            if (threadIdx.x == 0) ls.qv = ld_volatile_u64(&cout->q);
             __syncthreads();
-            qv = lvl[4];
         }
-        mu -= in_new;
-        nf = n_new;
-        mf = mf_new;
         cur ^= 1;
         dir = next;
     }

@@ -249,45 +249,48 @@ __device__ __forceinline__ int32_t warp_find_entry(const int32_t* qp, int32_t co
     return lo;
 }
 
-// Edges of one push step: the frontier vertex u, child v and CSR position k
-// (for edge values) of each lane's edges.
-struct PushStep {
-    int32_t u[kPushIlp];
-    int32_t v[kPushIlp];
-    int32_t k[kPushIlp];
+// Edges of one push step of I edges per lane: the frontier vertex u, child v and
+// CSR position k (for edge values) of each lane's edges.
+template <int I>
+struct PushStepT {
+    int32_t u[I];
+    int32_t v[I];
+    int32_t k[I];
 };
 
 // Walks a warp's edge range: maps edge ids to (queue entry, child) with a window
 // of the next 32 * kPushIlp entry boundaries (lane holds entries k+1+lane+32t).
 // Every entry has at least one edge, so the boundaries inside one step are all in
 // the window; it is reloaded only once a step could reach past its last boundary.
-struct PushCursor {
+template <int I>
+struct PushCursorT {
+    static constexpr int kStep = 32 * I;  // edges of one step
     int32_t k;
     int32_t wlast;
-    int32_t wv[kPushIlp];
+    int32_t wv[I];
 
-    // Maps the edges [base, base + kPushStep) of one step (lane t-th slot: edge
+    // Maps the edges [base, base + kStep) of one step (lane t-th slot: edge
     // base + 32 t + lane) to their queue entries and loads each edge's frontier
     // vertex u (-1 at or past e1) and d = (row start - prefix) of its entry, so that
     // the edge's CSR position is e + d.  The loads are issued, not waited for.
     __device__ __forceinline__ void map(const int32_t* q, const int32_t* qp, const int32_t* qd, uint32_t qcount,
-                                        int32_t base, int32_t e1, int32_t (&u)[kPushIlp], int32_t (&d)[kPushIlp]) {
+                                        int32_t base, int32_t e1, int32_t (&u)[I], int32_t (&d)[I]) {
         const int lane = threadIdx.x & 31;
-        if (wlast <= base + kPushStep - 1) {
+        if (wlast <= base + kStep - 1) {
 #pragma unroll
-            for (int t = 0; t < kPushIlp; ++t) {
+            for (int t = 0; t < I; ++t) {
                 const int32_t wi = k + 1 + lane + 32 * t;
                 wv[t] = wi < (int32_t)qcount ? qp[wi] : INT32_MAX;
             }
-            wlast = __shfl_sync(0xffffffffu, wv[kPushIlp - 1], 31);
+            wlast = __shfl_sync(0xffffffffu, wv[I - 1], 31);
         }
-        // occupancy of [base, base + kPushStep) by boundaries, one 32-bit word per lane-edge slot
-        uint32_t occ[kPushIlp];
+        // occupancy of [base, base + kStep) by boundaries, one 32-bit word per lane-edge slot
+        uint32_t occ[I];
 #pragma unroll
-        for (int m = 0; m < kPushIlp; ++m) {
+        for (int m = 0; m < I; ++m) {
             uint32_t c = 0;
 #pragma unroll
-            for (int t = 0; t < kPushIlp; ++t) {
+            for (int t = 0; t < I; ++t) {
                 const int32_t rel = wv[t] - base;  // wv <= INT32_MAX, base >= 0: no overflow
                 c |= (rel >= 32 * m && rel < 32 * (m + 1)) ? (1u << (rel - 32 * m)) : 0u;
             }
@@ -295,7 +298,7 @@ struct PushCursor {
         }
         uint32_t before = 0;
 #pragma unroll
-        for (int t = 0; t < kPushIlp; ++t) {
+        for (int t = 0; t < I; ++t) {
             const int32_t kk = k + (int32_t)(before + __popc(occ[t] & (0xffffffffu >> (31 - lane))));
             before += __popc(occ[t]);
             const int32_t e = base + 32 * t + lane;
@@ -309,14 +312,14 @@ struct PushCursor {
         k += (int32_t)before;
     }
 
-    __device__ __forceinline__ PushStep gather(const int32_t* out_col, const int32_t* q, const int32_t* qp,
+    __device__ __forceinline__ PushStepT<I> gather(const int32_t* out_col, const int32_t* q, const int32_t* qp,
                                                const int32_t* qd, uint32_t qcount, int32_t base, int32_t e1) {
         const int lane = threadIdx.x & 31;
-        int32_t u[kPushIlp], d[kPushIlp];
+        int32_t u[I], d[I];
         map(q, qp, qd, qcount, base, e1, u, d);
-        PushStep st;
+        PushStepT<I> st;
 #pragma unroll
-        for (int t = 0; t < kPushIlp; ++t) {
+        for (int t = 0; t < I; ++t) {
             st.u[t] = u[t];
             st.k[t] = u[t] >= 0 ? base + 32 * t + lane + d[t] : 0;
             st.v[t] = u[t] >= 0 ? __ldg(out_col + st.k[t]) : 0;
@@ -325,5 +328,8 @@ struct PushCursor {
     }
 };
 
+
+using PushStep = PushStepT<kPushIlp>;
+using PushCursor = PushCursorT<kPushIlp>;
 
 }  // namespace gbx
