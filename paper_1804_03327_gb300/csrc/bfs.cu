@@ -49,6 +49,7 @@ struct BfsArgs {
     const int32_t* in_ptr;
     const int32_t* in_col;
     const uint32_t* nz_in;
+    const uint32_t* multi_in;
     const int32_t* first_in;
     int32_t* depth;
     int32_t* parent;
@@ -63,7 +64,8 @@ struct BfsArgs {
     LevelRec* trace;
     int32_t* status;
     float alpha, beta;
-    int32_t heuristic, mode, early_exit, masking, operand_reuse, symmetric, need_indeg, trace_cap, probe, tile_words;
+    int32_t heuristic, mode, early_exit, masking, operand_reuse, symmetric, need_indeg, need_deg, trace_cap, probe,
+        tile_words;
     unsigned long long timeout_ns;
     unsigned int bar_parity;
 };
@@ -275,11 +277,31 @@ __device__ __forceinline__ int warp_scan(const int32_t* __restrict__ in_col, con
     return pos;
 }
 
-// A warp takes a tile of a.tile_words bitmap words, finds the rows the mask
-// lets through (unvisited, with in-edges), packs them in registers (per-word
-// popcount, warp scan, __fns) and processes them 32 * kPullIlp per round, kPullIlp
-// rows per lane probing in lockstep; rows longer than the probe depth are
-// finished by the whole warp, or by the whole grid when they are very long.
+// A warp takes a tile of a.tile_words bitmap words and finds the rows the mask
+// lets through (unvisited, with in-edges).  Pass 1 tests every such row's first
+// in-neighbour (the dense first_in array) against the frontier, kP1 rows per lane
+// in flight, packed in registers (per-word popcount, warp scan, __fns); most rows
+// of a power-law graph settle here.  Pass 2 takes the rows pass 1 left open that
+// have more in-neighbours, 32 * kPullIlp per round, kPullIlp rows per lane probing
+// in lockstep; rows longer than the probe depth are finished by the whole warp, or
+// by the whole grid when they are very long.
+#ifndef GBX_PULL_P1
+#define GBX_PULL_P1 4
+#endif
+constexpr int kP1 = GBX_PULL_P1;  // pass-1 rows per lane per round
+
+// Word j of a warp's tile holding candidate c of the packed list (excl: exclusive
+// prefix of the words' candidate counts, lane j holding word j's), and c's bit.
+__device__ __forceinline__ int cand_word(uint32_t excl, uint32_t c) {
+    int j = 0;
+#pragma unroll
+    for (int step = 16; step >= 1; step >>= 1) {
+        const uint32_t ev = __shfl_sync(0xffffffffu, excl, j + step);
+        if (ev <= c) j += step;
+    }
+    return j;
+}
+
 template <bool kHuge>
 __device__ __forceinline__ void pull_level(const BfsArgs& a, int32_t L, int vcur, bool use_fbm, bool append,
                                            const HugeRows& hr, Stage& st, unsigned long long* bsm, uint32_t* snew,
@@ -292,20 +314,74 @@ __device__ __forceinline__ void pull_level(const BfsArgs& a, int32_t L, int vcur
     const uint32_t* tbm = use_fbm ? a.fbm : vprev;
     const int32_t tw = a.tile_words;
     const int32_t ntiles = (a.nwords + tw - 1) / tw;
+    const bool want_deg = a.need_deg != 0;
     for (int32_t tile = gwarp; tile < ntiles; tile += nwarps) {
         const int32_t w = tile * tw + lane;
         const bool wok = lane < tw && w < a.nwords;
         const uint32_t cw = wok ? vprev[w] : 0xffffffffu;
         const uint32_t nz = wok ? a.nz_in[w] : 0u;
         const uint32_t cand = a.masking ? (~cw & nz) : nz;
-        const uint32_t cntw = __popc(cand);
+        snew[lane] = 0u;
+        __syncwarp();
+        const uint32_t cntc = __popc(cand);
+        const uint32_t inclc = warp_inclusive_sum(cntc);
+        const uint32_t totalc = __shfl_sync(0xffffffffu, inclc, 31);
+        // a tile with no more candidates than one pass-2 round takes them all there (one pass, whose
+        // row offsets load with the first in-neighbour); fuller tiles run pass 1 first
+        const bool two_pass = totalc > 32u * kPullIlp;
+        // ---- pass 1: the first in-neighbour of every candidate row
+        if (two_pass) {
+            const uint32_t total = totalc;
+            const uint32_t excl = inclc - cntc;
+            acc.exam += cntc;  // every candidate examines its first in-neighbour
+            for (uint32_t base = 0; base < total; base += 32 * kP1) {
+                int32_t i[kP1], f0[kP1];
+#pragma unroll
+                for (int r = 0; r < kP1; ++r) {
+                    const uint32_t c = base + 32 * r + lane;
+                    const int j = cand_word(excl, c);
+                    const uint32_t cj = __shfl_sync(0xffffffffu, cand, j);
+                    const uint32_t ej = __shfl_sync(0xffffffffu, excl, j);
+                    i[r] = c < total ? ((tile * tw + j) << 5) + (int)__fns(cj, 0u, (int)(c - ej) + 1) : -1;
+                }
+#pragma unroll
+                for (int r = 0; r < kP1; ++r) f0[r] = i[r] >= 0 ? __ldg(a.first_in + i[r]) : -1;
+#pragma unroll
+                for (int r = 0; r < kP1; ++r) {
+                    const int j = (i[r] >> 5) - tile * tw;  // word of the tile (any lane when i < 0)
+                    const int bp = i[r] & 31;
+                    const uint32_t cwj = __shfl_sync(0xffffffffu, cw, j & 31);
+                    const bool hit = f0[r] >= 0 && bit_test(tbm, f0[r]);
+                    if (hit) atomicOr(snew + j, 1u << bp);
+                    // without masking a visited row may find a parent too; only unvisited rows are new
+                    const bool isnew = hit && !((cwj >> bp) & 1u);
+                    if (isnew) {
+                        a.depth[i[r]] = L + 1;
+                        if (a.parent) a.parent[i[r]] = f0[r];
+                        acc.n_new += 1;
+                        if (want_deg) {  // m_f and m_u of the level (trace, Beamer's rule)
+                            const int32_t rs = __ldg(a.in_ptr + i[r]), re = __ldg(a.in_ptr + i[r] + 1);
+                            const int32_t od = a.symmetric ? re - rs
+                                                           : __ldg(a.out_ptr + i[r] + 1) - __ldg(a.out_ptr + i[r]);
+                            acc.mf += (uint32_t)od;
+                            acc.indeg += (uint32_t)(re - rs);
+                        }
+                    }
+                    if (append) st.put(isnew, i[r]);
+                }
+            }
+        }
+        __syncwarp();
+        const uint32_t f1 = snew[lane];  // rows of my word that pass 1 found
+        // ---- pass 2: rows with more in-neighbours that pass 1 did not settle
+        const uint32_t multi = wok ? a.multi_in[w] : 0u;
+        const uint32_t sv = two_pass ? cand & multi & (a.early_exit ? ~f1 : 0xffffffffu) : cand;
+        const uint32_t cntw = __popc(sv);
         const uint32_t incl = warp_inclusive_sum(cntw);
         const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
         const uint32_t excl = incl - cntw;
-        snew[lane] = 0u;
-        __syncwarp();
         for (uint32_t base = 0; base < total; base += 32 * kPullIlp) {
-            bool mine[kPullIlp], found[kPullIlp], done[kPullIlp];
+            bool mine[kPullIlp], found[kPullIlp], found1[kPullIlp], done[kPullIlp];
             int jw[kPullIlp], bitpos[kPullIlp];
             uint32_t cwj[kPullIlp];
             int32_t i[kPullIlp], beg[kPullIlp], end[kPullIlp], k[kPullIlp], par[kPullIlp];
@@ -314,42 +390,36 @@ __device__ __forceinline__ void pull_level(const BfsArgs& a, int32_t L, int vcur
             for (int r = 0; r < kPullIlp; ++r) {
                 const uint32_t c = base + 32 * r + lane;
                 mine[r] = c < total;
-                // word of candidate c: the largest j with excl_j <= c
-                int j = 0;
-#pragma unroll
-                for (int step = 16; step >= 1; step >>= 1) {
-                    const uint32_t ev = __shfl_sync(0xffffffffu, excl, j + step);
-                    if (ev <= c) j += step;
-                }
+                const int j = cand_word(excl, c);
                 jw[r] = j;
-                const uint32_t cj = __shfl_sync(0xffffffffu, cand, j);
+                const uint32_t cj = __shfl_sync(0xffffffffu, sv, j);
                 const uint32_t ej = __shfl_sync(0xffffffffu, excl, j);
+                const uint32_t f1j = __shfl_sync(0xffffffffu, f1, j);
                 cwj[r] = __shfl_sync(0xffffffffu, cw, j);
                 bitpos[r] = mine[r] ? (int)__fns(cj, 0u, (int)(c - ej) + 1) : 0;
                 i[r] = ((tile * tw + j) << 5) + bitpos[r];
-                found[r] = false;
+                // only without early exit does pass 2 see rows pass 1 already found
+                found1[r] = mine[r] && ((f1j >> bitpos[r]) & 1u);
+                found[r] = found1[r];
                 done[r] = false;
-                par[r] = -1;
                 exam[r] = 0;
             }
-            int32_t f0[kPullIlp];
 #pragma unroll
             for (int r = 0; r < kPullIlp; ++r) {
                 beg[r] = mine[r] ? __ldg(a.in_ptr + i[r]) : 0;
                 end[r] = mine[r] ? __ldg(a.in_ptr + i[r] + 1) : 0;
-                f0[r] = mine[r] ? __ldg(a.first_in + i[r]) : -1;
+                par[r] = (mine[r] && (!two_pass || found1[r])) ? __ldg(a.first_in + i[r]) : -1;
             }
-            // first probe from the dense first-neighbour array (same ascending order)
 #pragma unroll
             for (int r = 0; r < kPullIlp; ++r) {
-                k[r] = beg[r];
-                if (f0[r] >= 0) {
+                k[r] = beg[r] + 1;  // the first in-neighbour is examined (by pass 1, or right here)
+                if (!two_pass && mine[r]) {
                     exam[r] = 1;
-                    k[r] = beg[r] + 1;
-                    if (bit_test(tbm, f0[r])) {
+                    if (bit_test(tbm, par[r])) {  // a candidate has in-edges: par holds its first
                         found[r] = true;
-                        par[r] = f0[r];
                         done[r] = a.early_exit != 0;
+                    } else {
+                        par[r] = -1;
                     }
                 }
             }
@@ -446,26 +516,20 @@ __device__ __forceinline__ void pull_level(const BfsArgs& a, int32_t L, int vcur
             }
 #pragma unroll
             for (int r = 0; r < kPullIlp; ++r) {
-                // without masking a visited row may find a parent too; only unvisited rows are new
-                const bool isnew = found[r] && !((cwj[r] >> bitpos[r]) & 1u);
-                int32_t rs = 0, od = 0;
+                // new: found here, not by pass 1, and not visited before (rows without masking may be)
+                const bool isnew = found[r] && !found1[r] && !((cwj[r] >> bitpos[r]) & 1u);
                 if (isnew) {
                     atomicOr(snew + jw[r], 1u << bitpos[r]);
                     a.depth[i[r]] = L + 1;
                     if (a.parent) a.parent[i[r]] = par[r];
-                    if (a.symmetric) {
-                        rs = beg[r];
-                        od = end[r] - beg[r];
-                    } else {
-                        rs = __ldg(a.out_ptr + i[r]);
-                        od = __ldg(a.out_ptr + i[r] + 1) - rs;
-                    }
+                    const int32_t od = a.symmetric ? end[r] - beg[r]
+                                                   : __ldg(a.out_ptr + i[r] + 1) - __ldg(a.out_ptr + i[r]);
                     acc.n_new += 1;
-                    acc.mf += (unsigned long long)od;
-                    acc.indeg += (unsigned long long)(end[r] - beg[r]);
+                    acc.mf += (uint32_t)od;
+                    acc.indeg += (uint32_t)(end[r] - beg[r]);
                 }
                 acc.exam += exam[r];
-                if (append) st.put(isnew && od > 0, i[r]);
+                if (append) st.put(isnew, i[r]);
             }
         }
         __syncwarp();
@@ -547,8 +611,8 @@ __device__ GBX_PULL_HUGE_INLINE void pull_huge(const BfsArgs& a, int32_t L, int 
                 if (a.parent) a.parent[i] = par;
                 od = a.symmetric ? rend - rbeg : __ldg(a.out_ptr + i + 1) - __ldg(a.out_ptr + i);
                 acc.n_new += 1;
-                acc.mf += (unsigned long long)od;
-                acc.indeg += (unsigned long long)(rend - rbeg);
+                acc.mf += (uint32_t)od;
+                acc.indeg += (uint32_t)(rend - rbeg);
             }
         }
         if (append) st.put(isnew && od > 0, i);
@@ -565,7 +629,7 @@ __device__ __forceinline__ void pull_huge_exam(const BfsArgs& a, const HugeRows&
         const int32_t i = code < 0 ? ~code : code;
         const int32_t fk = hr.first[e];
         const int32_t stop = fk != INT32_MAX ? fk + 1 : __ldg(a.in_ptr + i + 1);
-        acc.exam += (unsigned long long)(stop - hr.k[e]);
+        acc.exam += (uint32_t)(stop - hr.k[e]);
     }
 }
 
@@ -867,6 +931,7 @@ static gbx_status launch_bfs(Graph* G, int32_t source, int32_t* depth, int32_t* 
     a.in_ptr = G->in_ptr;
     a.in_col = G->in_col;
     a.nz_in = G->nz_in;
+    a.multi_in = G->multi_in;
     a.first_in = G->first_in;
     a.depth = depth;
     a.parent = parent;
@@ -892,6 +957,7 @@ static gbx_status launch_bfs(Graph* G, int32_t source, int32_t* depth, int32_t* 
     a.operand_reuse = d.operand_reuse ? 1 : 0;
     a.symmetric = G->symmetric;
     a.need_indeg = (!G->symmetric && (d.trace || d.heuristic == GBX_HEUR_BEAMER)) ? 1 : 0;
+    a.need_deg = (d.trace || d.heuristic == GBX_HEUR_BEAMER) ? 1 : 0;  // m_f and m_u of the found rows
     a.trace_cap = kTraceCap;
     a.probe = d.pull_probe > 0 ? (d.pull_probe + 3) / 4 * 4 : kProbe;
     a.timeout_ns = wait_timeout_ns();

@@ -14,8 +14,10 @@ namespace gbx {
 constexpr int kPushIlp = GBX_PUSH_ILP;  // edges per lane per push step (independent chains)
 constexpr int kPushStep = 32 * kPushIlp;
 
+// One thread's counts of a level (each stays below 2^32: a level finds at most n
+// vertices and examines at most nnz < 2^31 entries); blocks add them up in 64 bits.
 struct Acc {
-    unsigned long long n_new = 0, mf = 0, indeg = 0, exam = 0;
+    uint32_t n_new = 0, mf = 0, indeg = 0, exam = 0;
 };
 
 // Next-frontier appends are staged per warp in shared memory and published
@@ -64,11 +66,11 @@ struct Stage {
         if (count_degrees) {
 #pragma unroll
             for (int t = 0; t < R; ++t) {
-                acc->mf += (unsigned long long)od[t];
+                acc->mf += (uint32_t)od[t];
                 if (need_indeg)
-                    acc->indeg += v[t] >= 0 ? (unsigned long long)(__ldg(in_ptr + v[t] + 1) - __ldg(in_ptr + v[t])) : 0ull;
+                    acc->indeg += v[t] >= 0 ? (uint32_t)(__ldg(in_ptr + v[t] + 1) - __ldg(in_ptr + v[t])) : 0u;
                 else
-                    acc->indeg += (unsigned long long)od[t];
+                    acc->indeg += (uint32_t)od[t];
             }
         }
         uint32_t keep[R];
@@ -127,11 +129,11 @@ struct Stage {
         if (count_degrees) {
 #pragma unroll
             for (int t = 0; t < R; ++t) {
-                acc->mf += (unsigned long long)od[t];
+                acc->mf += (uint32_t)od[t];
                 if (need_indeg)
-                    acc->indeg += v[t] >= 0 ? (unsigned long long)(__ldg(in_ptr + v[t] + 1) - __ldg(in_ptr + v[t])) : 0ull;
+                    acc->indeg += v[t] >= 0 ? (uint32_t)(__ldg(in_ptr + v[t] + 1) - __ldg(in_ptr + v[t])) : 0u;
                 else
-                    acc->indeg += (unsigned long long)od[t];
+                    acc->indeg += (uint32_t)od[t];
             }
         }
         uint32_t keep[R];

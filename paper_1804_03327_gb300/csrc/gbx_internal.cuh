@@ -128,6 +128,7 @@ struct Graph {
     int32_t* in_col = nullptr;
     uint32_t* nz_in = nullptr;   // bit v set iff in-degree(v) > 0
     uint32_t* nz_out = nullptr;  // bit v set iff out-degree(v) > 0
+    uint32_t* multi_in = nullptr;  // bit v set iff in-degree(v) > 1
     // first (smallest) in-neighbour of each row, -1 if none: the first probe of a
     // pull row reads this dense array instead of a random sector of in_col
     int32_t* first_in = nullptr;

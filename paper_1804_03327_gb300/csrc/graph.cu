@@ -76,11 +76,13 @@ __global__ void first_neighbour_kernel(const int32_t* __restrict__ row_ptr, cons
         first[i] = row_ptr[i + 1] > row_ptr[i] ? col[row_ptr[i]] : -1;
 }
 
-__global__ void nonzero_rows_kernel(const int32_t* __restrict__ row_ptr, int32_t n, uint32_t* __restrict__ bm) {
+// bm bit i set iff row i has at least min_len entries.
+__global__ void nonzero_rows_kernel(const int32_t* __restrict__ row_ptr, int32_t n, int32_t min_len,
+                                    uint32_t* __restrict__ bm) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nw32 = ((int64_t)n + 31) & ~(int64_t)31;
     if (i - (threadIdx.x & 31) >= nw32) return;
-    const bool nz = i < n && row_ptr[i + 1] > row_ptr[i];
+    const bool nz = i < n && row_ptr[i + 1] - row_ptr[i] >= min_len;
     const uint32_t word = __ballot_sync(0xffffffffu, nz);
     if ((threadIdx.x & 31) == 0) bm[i >> 5] = word;
 }
@@ -176,6 +178,7 @@ static void graph_release(Graph* g) {
     f(g->out_ptr);
     f(g->out_col);
     f(g->nz_in);
+    f(g->multi_in);
     if (g->nz_out != g->nz_in) f(g->nz_out);
     if (g->first_out != g->first_in) f(g->first_out);
     f(g->first_in);
@@ -299,12 +302,14 @@ static gbx_status build_impl(Graph* g, int32_t n, int64_t m, const int32_t* src,
     if (st != GBX_OK) return st;
     GBX_CUDA_TRY(cudaMalloc((void**)&g->nz_in, sizeof(uint32_t) * ((size_t)g->nwords + 1)));
     const int64_t nw32 = ((int64_t)n + 31) & ~(int64_t)31;
-    nonzero_rows_kernel<<<div_up(nw32, 256), 256, 0, s>>>(g->in_ptr, n, g->nz_in);
+    nonzero_rows_kernel<<<div_up(nw32, 256), 256, 0, s>>>(g->in_ptr, n, 1, g->nz_in);
+    GBX_CUDA_TRY(cudaMalloc((void**)&g->multi_in, sizeof(uint32_t) * ((size_t)g->nwords + 1)));
+    nonzero_rows_kernel<<<div_up(nw32, 256), 256, 0, s>>>(g->in_ptr, n, 2, g->multi_in);
     if (sym) {
         g->nz_out = g->nz_in;
     } else {
         GBX_CUDA_TRY(cudaMalloc((void**)&g->nz_out, sizeof(uint32_t) * ((size_t)g->nwords + 1)));
-        nonzero_rows_kernel<<<div_up(nw32, 256), 256, 0, s>>>(g->out_ptr, n, g->nz_out);
+        nonzero_rows_kernel<<<div_up(nw32, 256), 256, 0, s>>>(g->out_ptr, n, 1, g->nz_out);
     }
     GBX_CUDA_TRY(cudaMalloc((void**)&g->first_in, sizeof(int32_t) * ((size_t)n + 1)));
     first_neighbour_kernel<<<grid_for(n), 256, 0, s>>>(g->in_ptr, g->in_col, n, g->first_in);

@@ -217,7 +217,7 @@ __device__ __forceinline__ void ms_pull(const MsArgs& a, int32_t L, unsigned lon
                     full &= unv[j] == nw;
                 }
                 any_new |= nw != 0ull;
-                acc.n_new += (unsigned long long)__popcll(nw);
+                acc.n_new += (uint32_t)__popcll(nw);
                 write_depth_word(a, c + j, nw, v, L + 1);
             }
         }
@@ -310,7 +310,7 @@ __device__ __forceinline__ void ms_push(const MsArgs& a, int32_t L, const int32_
                                 atomicOr(Fn + iv, gained);  // result unused: a reduction; T_next lists v
                             }
                             any = true;
-                            acc.n_new += (unsigned long long)__popcll(gained);
+                            acc.n_new += (uint32_t)__popcll(gained);
                             unsigned long long m = gained;
                             while (m) {
                                 const int b = __ffsll((long long)m) - 1;
@@ -363,7 +363,7 @@ __device__ __forceinline__ void ms_push_finalize(const MsArgs& a, int32_t L, uin
                 a.V[idx] = vv | nw;
                 Fn[idx] = nw;
                 full &= ((vv | nw) & lane_mask(a.S, w)) == lane_mask(a.S, w);
-                acc.n_new += (unsigned long long)__popcll(nw);
+                acc.n_new += (uint32_t)__popcll(nw);
                 any_new |= nw != 0ull;
                 unsigned long long m = nw;
                 while (m) {

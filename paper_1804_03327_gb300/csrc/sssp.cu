@@ -84,7 +84,7 @@ __device__ __forceinline__ void sssp_push(const SsspArgs& a, int32_t L, int cur,
             }
 #pragma unroll
             for (int t = 0; t < kPushIlp; ++t) {
-                acc.exam += st.u[t] >= 0 ? 1ull : 0ull;
+                acc.exam += st.u[t] >= 0 ? 1u : 0u;
                 if (queued[t]) acc.n_new += 1;
                 stg.put(queued[t], st.v[t]);
             }
@@ -131,7 +131,7 @@ __device__ __forceinline__ void sssp_pull(const SsspArgs& a, Acc& acc) {
         }
         const uint32_t word = __ballot_sync(0xffffffffu, better);
         if (lane == 0) a.chg[wd] = word;
-        acc.exam += (unsigned long long)(end - beg);
+        acc.exam += (uint32_t)(end - beg);
         if (better) acc.n_new += 1;
     }
 }

@@ -277,7 +277,7 @@ def test_bounded_wait_times_out_and_context_survives():
 @pytest.mark.slow
 def test_full_size_rmat22_all_workload_sources():
     """RMAT scale 22 (edge factor 16), the benchmark's 64 sources with the
-    descriptor the benchmark autotunes on 16 other sources: every source's depths
+    descriptor the benchmark autotunes on 32 other sources: every source's depths
     bit-exact against the oracle (run one source per host thread: ctypes releases
     the GIL in the C BFS), parents valid on a sample."""
     from concurrent.futures import ThreadPoolExecutor
@@ -288,7 +288,7 @@ def test_full_size_rmat22_all_workload_sources():
     nn, nnz, _ = g.info()
     assert nnz == og.nnz
     srcs = [int(x) for x in synth.sources(n, s, d, 64, seed=1)]
-    tuned, _ = gbx.autotune(g, gbx.TUNE_BFS, synth.sources(n, s, d, 16, seed=101))
+    tuned, _ = gbx.autotune(g, gbx.TUNE_BFS, synth.sources(n, s, d, 32, seed=101))
     with ThreadPoolExecutor(os.cpu_count() or 1) as ex:
         wants = list(ex.map(lambda x: oracle.bfs(og, x)[0], srcs))
     for k, src in enumerate(srcs):
