@@ -92,8 +92,11 @@ __device__ __forceinline__ void flush_acc(const Acc& acc, LevelCtr* cout, bool w
 #endif
 constexpr int kBfsIlp = GBX_BFS_PUSH_ILP;  // edges per lane and step (2 needs more than the 64 registers)
 constexpr int kBfsStep = 32 * kBfsIlp;
+// stamp: write depth and parent of the claimed children (level 0 leaves them to the
+// start of level 1, when the concurrently initialised outputs are complete).
 __device__ __forceinline__ void push_level(const BfsArgs& a, int32_t L, int cur, int vcur, uint32_t qcount,
-                                           uint32_t qedges, Stage& stg, unsigned long long* bsm, Acc& acc) {
+                                           uint32_t qedges, Stage& stg, unsigned long long* bsm, Acc& acc,
+                                           bool stamp) {
     const int lane = threadIdx.x & 31;
     const int gwarp = (int)((blockIdx.x * kBfsThreads + threadIdx.x) >> 5);
     const int nwarps = (int)((gridDim.x * kBfsThreads) >> 5);
@@ -121,8 +124,10 @@ __device__ __forceinline__ void push_level(const BfsArgs& a, int32_t L, int cur,
                     const bool claimed = now.u[t] >= 0 && !(__ldca(vis + (now.v[t] >> 5)) & bit) &&
                                          !(atomicOr(vis + (now.v[t] >> 5), bit) & bit);
                     if (claimed) {
-                        a.depth[now.v[t]] = L + 1;
-                        if (a.parent) a.parent[now.v[t]] = now.u[t];
+                        if (stamp) {
+                            a.depth[now.v[t]] = L + 1;
+                            if (a.parent) a.parent[now.v[t]] = now.u[t];
+                        }
                         acc.n_new += 1;
                     }
                     stg.put(claimed, now.v[t]);
@@ -175,8 +180,10 @@ __device__ __forceinline__ void push_level(const BfsArgs& a, int32_t L, int cur,
             for (int t = 0; t < kBfsIlp; ++t) {
                 const bool claimed = u3[t] >= 0 && !(old[t] & (1u << (v3[t] & 31)));
                 if (claimed) {
-                    a.depth[v3[t]] = L + 1;
-                    if (a.parent) a.parent[v3[t]] = u3[t];
+                    if (stamp) {
+                        a.depth[v3[t]] = L + 1;
+                        if (a.parent) a.parent[v3[t]] = u3[t];
+                    }
                     acc.n_new += 1;
                 }
                 stg.put(claimed, v3[t]);
@@ -754,9 +761,15 @@ __global__ void __launch_bounds__(kBfsThreads, kBfsMinBlocks) bfs_kernel(BfsArgs
     // an error of an earlier launch not yet read by the host: this launch does nothing
     const int pending = threadIdx.x == 0 ? ld_volatile_i32(a.status + ST_ERROR) : 0;
     unsigned long long t_mark = kTrace && gtid == 0 ? global_timer_ns() : 0ull;
-    // Algorithm 1, lines 2-5: f = e_s, v = {s}; outputs initialised
-    fill_outputs(a.depth, a.n, -1, s, 0, gtid, gstride);
-    if (a.parent) fill_outputs(a.parent, a.n, -1, s, s, gtid, gstride);
+    // Algorithm 1, lines 2-5: f = e_s, v = {s}; outputs initialised.  When level 0 pushes,
+    // its claims (the source's out-neighbours, all new) write no outputs, so the outputs
+    // are initialised during level 0 instead, hidden behind its latency, and level 1
+    // starts by stamping the source's out-neighbours (depth 1, parent s).
+    const bool fill_in_level0 = a.mode != GBX_DIR_PULL;
+    if (!fill_in_level0) {
+        fill_outputs(a.depth, a.n, -1, s, 0, gtid, gstride);
+        if (a.parent) fill_outputs(a.parent, a.n, -1, s, s, gtid, gstride);
+    }
     for (long long w = gtid; w < a.nwords; w += gstride) a.vis[0][w] = w == (s >> 5) ? 1u << (s & 31) : 0u;
     const int32_t s_rs = __ldg(a.out_ptr + s);
     const int32_t s_od = __ldg(a.out_ptr + s + 1) - s_rs;
@@ -816,7 +829,12 @@ __global__ void __launch_bounds__(kBfsThreads, kBfsMinBlocks) bfs_kernel(BfsArgs
         Stage st{stage_mem + wib, 0, cout, a.q[cur ^ 1], a.qp[cur ^ 1], a.qd[cur ^ 1],
                  a.out_ptr, a.in_ptr, dir == DIR_PUSH, a.need_indeg, &acc};
         if (dir == DIR_PUSH) {
-            push_level(a, L, cur, vcur, qcount, qedges, st, stage_sum, acc);
+            const bool first = L == 0 && fill_in_level0;
+            push_level(a, L, cur, vcur, qcount, qedges, st, stage_sum, acc, !first);
+            if (first) {
+                fill_outputs(a.depth, a.n, -1, s, 0, gtid, gstride);
+                if (a.parent) fill_outputs(a.parent, a.n, -1, s, s, gtid, gstride);
+            }
             appended = true;
         } else {
             const bool use_fbm = !a.operand_reuse;
@@ -870,6 +888,15 @@ __global__ void __launch_bounds__(kBfsThreads, kBfsMinBlocks) bfs_kernel(BfsArgs
         if (threadIdx.x == 0) level_end<kTrace>(a, L, dir, lvl, ls);
         __syncthreads();
         if (ls.stop) return;
+        if (L == 0 && fill_in_level0) {  // the outputs are initialised everywhere now
+            for (long long k = gtid; k < s_od; k += gstride) {
+                const int32_t v = __ldg(a.out_col + s_rs + k);
+                if (v != s) {
+                    a.depth[v] = 1;
+                    if (a.parent) a.parent[v] = s;
+                }
+            }
+        }
         const int next = ls.next;
         if (dir == DIR_PULL) vcur ^= 1;
         if (dir == DIR_PULL && next == DIR_PUSH && !appended) {
