@@ -100,6 +100,7 @@ struct Workspace {
     // batched multi-source BFS scratch (allocated on first use, grown as needed)
     unsigned long long* msV = nullptr;                     // visited lanes [n][W]
     unsigned long long* msF[3] = {nullptr, nullptr, nullptr};  // lanes found per level, rotating [n][W]
+    unsigned long long* msP = nullptr;  // depth bit planes: 5 x [n][W] (bits 0-3 of depths below 16, overflow)
     int32_t* msT = nullptr;                                    // vertices a wide push level touched [n]
     int64_t ms_t_cap = 0;                                      // entries msT holds
     int64_t ms_cap_words = 0;

@@ -161,6 +161,7 @@ void workspace_release(Workspace& w) {
     f(w.flag);
     f(w.msV);
     for (auto& p : w.msF) f(p);
+    f(w.msP);
     f(w.msT);
     f(w.ms_src);
     if (w.ms_src_pinned) cudaFreeHost(w.ms_src_pinned);

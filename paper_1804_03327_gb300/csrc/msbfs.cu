@@ -23,8 +23,12 @@
 //   pull (Eq 4 lane-wise, masking + early exit + operand reuse): every vertex with
 //     an unvisited lane ORs V of its in-neighbours (V is the state before this
 //     level) and stops as soon as every unvisited lane is covered; new = acc & ~V.
-// New lanes get depth L + 1; depth writes are transposed through the warp so that
-// 32 consecutive vertices of one lane are one coalesced store.
+// New lanes get depth L + 1.  Depths are not stored as they are found (2-byte
+// stores scattered over S rows leave partial sectors that are evicted and merged
+// again level after level): a depth below 16 is recorded as bits in four per-vertex
+// planes of lane words (plane p holds bit p), larger ones are stored at once, and
+// after the last level one pass emits every other entry of the S rows exactly once,
+// coalesced along the vertices (-1 where a lane never arrived).
 #include "frontier.cuh"
 #include "gbx_internal.cuh"
 
@@ -40,6 +44,7 @@ constexpr int kMsThreads = 512;
 constexpr int kMsOcc = 2;
 constexpr int kMsOccLean = 3;
 constexpr int kMsProbe = 8;  // default in-neighbours a lane scans alone before the warp takes over
+constexpr int kMsPlanes = 4;  // depth bit planes: bit p of depths below 16
 
 struct MsArgs {
     int32_t n, S, W, nwords;
@@ -51,6 +56,7 @@ struct MsArgs {
     const uint32_t* nz_in;
     unsigned long long* V;
     unsigned long long* Fb[3];  // rotating found-lane buffers
+    unsigned long long* P[4];   // depth bit planes (see record_depth)
     uint32_t* D;                // all lanes visited
     uint32_t* Tb[3];            // rotating "listed" bitmaps
     int32_t* tlist;             // vertices touched by a wide push level
@@ -93,23 +99,65 @@ __device__ __forceinline__ void store_depth(const MsArgs& a, int32_t lane_b, int
         static_cast<int32_t*>(a.depth)[idx] = d;
 }
 
-// Depth writes for one word of new lanes, transposed through the warp: for each
-// lane bit set anywhere in the warp, the lanes holding it store together.
-__device__ __forceinline__ void write_depth_word(const MsArgs& a, int32_t w, unsigned long long nw, int32_t v,
-                                                 int32_t d) {
-    const uint32_t lo = __reduce_or_sync(0xffffffffu, (uint32_t)nw);
-    const uint32_t hi = __reduce_or_sync(0xffffffffu, (uint32_t)(nw >> 32));
-    uint32_t m = lo;
-    while (m) {
-        const int b = __ffs(m) - 1;
-        m &= m - 1;
-        if ((nw >> b) & 1ull) store_depth(a, w * 64 + b, v, d);
+// Records depth d for the lanes nw of word w of vertex v.  Depths below 16 go to
+// the bit planes (atomically when several edges may record lanes of one word in the
+// same level, as the one-phase push does); larger ones are stored now.  A visited
+// lane with no plane bit is either its own source (depth 0) or such a deep one,
+// which the emission pass tells apart by the source.
+__device__ __forceinline__ void record_depth(const MsArgs& a, int32_t v, int32_t w, unsigned long long nw, int32_t d,
+                                             bool atomic) {
+    if (!nw) return;
+    if (d < 16) {
+        const size_t iv = (size_t)v * a.W + w;
+#pragma unroll
+        for (int p = 0; p < kMsPlanes; ++p) {
+            if (!((d >> p) & 1)) continue;
+            if (atomic)
+                atomicOr(a.P[p] + iv, nw);
+            else
+                a.P[p][iv] |= nw;
+        }
+        return;
     }
-    m = hi;
+    unsigned long long m = nw;
     while (m) {
-        const int b = __ffs(m) - 1;
+        const int b = __ffsll((long long)m) - 1;
         m &= m - 1;
-        if ((nw >> (32 + b)) & 1ull) store_depth(a, w * 64 + 32 + b, v, d);
+        store_depth(a, w * 64 + b, v, d);
+    }
+}
+
+// After the last level: every (lane, vertex) entry of the output rows, once.  A warp
+// takes 32 consecutive vertices and one lane word; for each of the word's lanes the 32
+// entries are one coalesced store.  Lanes never visited get -1; lanes found at depth
+// 16 or more were stored when found and are left alone.
+__device__ __forceinline__ void emit_depths(const MsArgs& a) {
+    const int lane = threadIdx.x & 31;
+    const long long gwarp = ((long long)blockIdx.x * kMsThreads + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * kMsThreads) >> 5;
+    const int32_t nvb = (a.n + 31) >> 5;
+    const int32_t wl = (a.S + 63) >> 6;  // words holding real lanes
+    const long long items = (long long)nvb * wl;
+    for (long long it = gwarp; it < items; it += nwarps) {
+        const int32_t vb = (int32_t)(it / wl), w = (int32_t)(it - (long long)vb * wl);
+        const int32_t v = (vb << 5) + lane;
+        const bool ok = v < a.n;
+        const size_t iv = (size_t)(ok ? v : 0) * a.W + w;
+        const unsigned long long vis = ok ? a.V[iv] : 0ull;
+        const unsigned long long p0 = ok ? a.P[0][iv] : 0ull, p1 = ok ? a.P[1][iv] : 0ull;
+        const unsigned long long p2 = ok ? a.P[2][iv] : 0ull, p3 = ok ? a.P[3][iv] : 0ull;
+        const unsigned long long any = p0 | p1 | p2 | p3;
+        const int nb = a.S - w * 64 < 64 ? a.S - w * 64 : 64;
+        for (int b = 0; b < nb; ++b) {
+            if (!ok) continue;
+            int32_t d = -1;
+            if ((vis >> b) & 1ull) {
+                if (!((any >> b) & 1ull) && __ldg(a.src + w * 64 + b) != v) continue;  // deep: already stored
+                d = (int32_t)(((p0 >> b) & 1ull) | (((p1 >> b) & 1ull) << 1) | (((p2 >> b) & 1ull) << 2) |
+                              (((p3 >> b) & 1ull) << 3));
+            }
+            store_depth(a, w * 64 + b, v, d);
+        }
     }
 }
 
@@ -218,7 +266,7 @@ __device__ __forceinline__ void ms_pull(const MsArgs& a, int32_t L, unsigned lon
                 }
                 any_new |= nw != 0ull;
                 acc.n_new += (uint32_t)__popcll(nw);
-                write_depth_word(a, c + j, nw, v, L + 1);
+                if (mine) record_depth(a, v, c + j, nw, L + 1, false);
             }
         }
         if (sink && full) atomicOr(a.D + (v >> 5), 1u << (v & 31));
@@ -311,12 +359,7 @@ __device__ __forceinline__ void ms_push(const MsArgs& a, int32_t L, const int32_
                             }
                             any = true;
                             acc.n_new += (uint32_t)__popcll(gained);
-                            unsigned long long m = gained;
-                            while (m) {
-                                const int b = __ffsll((long long)m) - 1;
-                                m &= m - 1;
-                                store_depth(a, (c + j) * 64 + b, v, L + 1);
-                            }
+                            record_depth(a, v, c + j, gained, L + 1, true);
                         }
                     }
                     (void)any;
@@ -365,12 +408,7 @@ __device__ __forceinline__ void ms_push_finalize(const MsArgs& a, int32_t L, uin
                 full &= ((vv | nw) & lane_mask(a.S, w)) == lane_mask(a.S, w);
                 acc.n_new += (uint32_t)__popcll(nw);
                 any_new |= nw != 0ull;
-                unsigned long long m = nw;
-                while (m) {
-                    const int b = __ffsll((long long)m) - 1;
-                    m &= m - 1;
-                    store_depth(a, w * 64 + b, v, L + 1);
-                }
+                record_depth(a, v, w, nw, L + 1, false);
             }
             Tn[v >> 5] = 0u;
             if (full) atomicOr(a.D + (v >> 5), 1u << (v & 31));
@@ -408,35 +446,21 @@ __global__ void __launch_bounds__(kMsThreads, kOcc) ms_bfs_kernel(MsArgs a) {
     unsigned int* barc = a.bar->count + a.bar_parity;
     unsigned int bar_round = 0;
     unsigned long long t_mark = gtid == 0 ? global_timer_ns() : 0ull;
-    // ---- init: V = F_k = 0, D = T_k = 0, depth = -1
+    // ---- init: V = F_k = 0, depth planes = 0, D = T_k = 0 (the output rows are written at the end)
     const size_t nw_total = (size_t)a.n * (size_t)a.W;
     for (size_t i = gtid; i < nw_total; i += gstride) {
         a.V[i] = 0ull;
         a.Fb[0][i] = 0ull;
         a.Fb[1][i] = 0ull;
         a.Fb[2][i] = 0ull;
+#pragma unroll
+        for (int p = 0; p < kMsPlanes; ++p) a.P[p][i] = 0ull;
     }
     for (long long w = gtid; w < a.nwords; w += gstride) {
         a.D[w] = 0u;
         a.Tb[0][w] = 0u;
         a.Tb[1][w] = 0u;
         a.Tb[2][w] = 0u;
-    }
-    const size_t nd = (size_t)a.S * (size_t)a.n;
-    if (a.rows) {
-        for (size_t i = gtid; i < nd; i += gstride) {
-            const size_t b = i / (size_t)a.n, v = i - b * (size_t)a.n;
-            if (a.depth16)
-                static_cast<int16_t*>(a.rows[b])[v] = (int16_t)-1;
-            else
-                static_cast<int32_t*>(a.rows[b])[v] = -1;
-        }
-    } else if (a.depth16) {
-        int16_t* d = static_cast<int16_t*>(a.depth);
-        for (size_t i = gtid; i < nd; i += gstride) d[i] = (int16_t)-1;
-    } else {
-        int32_t* d = static_cast<int32_t*>(a.depth);
-        for (size_t i = gtid; i < nd; i += gstride) d[i] = -1;
     }
     if (gtid == 0) {
         LevelCtr z = {};
@@ -451,8 +475,7 @@ __global__ void __launch_bounds__(kMsThreads, kOcc) ms_bfs_kernel(MsArgs a) {
     // ---- sources: lane b starts at src[b] with depth 0
     for (long long b = gtid; b < a.S; b += gstride) {
         const int32_t s = a.src[b];
-        atomicOr(a.V + (size_t)s * a.W + (b >> 6), 1ull << (b & 63));
-        store_depth(a, (int32_t)b, s, 0);
+        atomicOr(a.V + (size_t)s * a.W + (b >> 6), 1ull << (b & 63));  // depth 0: no plane bit
     }
     if (!grid_barrier(barc, gridDim.x, bar_round, a.status, a.timeout_ns)) return;
     // F = V for the (distinct) source vertices; they form the first active list
@@ -550,6 +573,7 @@ __global__ void __launch_bounds__(kMsThreads, kOcc) ms_bfs_kernel(MsArgs a) {
         }
         if (n_new == 0) {
             if (gtid == 0) a.status[ST_LEVELS] = L + 1;
+            emit_depths(a);
             return;
         }
         if (L + 1 >= a.n) {
@@ -566,7 +590,7 @@ gbx_status ms_reserve(Workspace& w, int32_t n, int32_t S, cudaStream_t s) {
     const int cw = w_raw >= 4 ? 4 : (w_raw >= 2 ? 2 : 1);
     const int64_t need = (int64_t)n * ((w_raw + cw - 1) / cw * cw);
     if (w.ms_cap_words < need) {
-        if (w.msV) {
+        if (w.msV || w.msP || w.msF[0] || w.msF[1] || w.msF[2]) {
             GBX_CUDA_TRY(cudaStreamSynchronize(s));
             cudaFree(w.msV);
             w.msV = nullptr;
@@ -574,11 +598,14 @@ gbx_status ms_reserve(Workspace& w, int32_t n, int32_t S, cudaStream_t s) {
                 cudaFree(p);
                 p = nullptr;
             }
+            cudaFree(w.msP);
+            w.msP = nullptr;
             w.ms_cap_words = 0;
         }
         GBX_CUDA_TRY(cudaMalloc((void**)&w.msV, sizeof(unsigned long long) * (size_t)need));
         for (auto& p : w.msF) GBX_CUDA_TRY(cudaMalloc((void**)&p, sizeof(unsigned long long) * (size_t)need));
-        w.ms_cap_words = need;
+        GBX_CUDA_TRY(cudaMalloc((void**)&w.msP, sizeof(unsigned long long) * (size_t)need * kMsPlanes));
+        w.ms_cap_words = need;  // only once every buffer exists
     }
     if (w.ms_t_cap < (int64_t)n + 1) {
         if (w.msT) {
@@ -596,7 +623,7 @@ gbx_status ms_reserve(Workspace& w, int32_t n, int32_t S, cudaStream_t s) {
 int64_t ms_scratch_bytes(int32_t n, int32_t S) {
     const int32_t w_raw = (S + 63) / 64;
     const int cw = w_raw >= 4 ? 4 : (w_raw >= 2 ? 2 : 1);
-    return 4ll * 8ll * (int64_t)n * ((w_raw + cw - 1) / cw * cw) + 4ll * ((int64_t)n + 1);
+    return (4ll + kMsPlanes) * 8ll * (int64_t)n * ((w_raw + cw - 1) / cw * cw) + 4ll * ((int64_t)n + 1);
 }
 
 template <int CW, int kOcc>
@@ -638,6 +665,7 @@ gbx_status ms_run(Graph* G, Workspace& w, int32_t S, const int32_t* src_dev, voi
     a.nz_in = G->nz_in;
     a.V = w.msV;
     for (int k = 0; k < 3; ++k) a.Fb[k] = w.msF[k];
+    for (int k = 0; k < kMsPlanes; ++k) a.P[k] = w.msP + (size_t)k * (size_t)G->n * (size_t)W;
     a.D = w.bm[2];
     a.Tb[0] = w.bm[3];
     a.Tb[1] = w.bm[0];

@@ -116,7 +116,8 @@ def test_server_int16_rows_and_admission():
 def test_server_memory_budget_limits_lanes():
     gs = graphs()
     n, s, d, og, g = gs["rmat12"]
-    one_word = 4 * 8 * n + 4 * (n + 1)  # scratch of a 64-lane batch (V, three found-lane buffers, touched list)
+    # scratch of a 64-lane batch: V, three found-lane buffers, four depth planes, touched list
+    one_word = 8 * 8 * n + 4 * (n + 1)
     srv = gbx.Server(max_batch=1024, slots=1, memory_budget=2 * one_word)
     gid = srv.add_graph(g)
     assert srv.lanes(gid) == 128
