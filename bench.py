@@ -69,6 +69,7 @@ def parse():
                         "K = -1: source 0 --repeat times, then each workload source once")
     p.add_argument("--repeat", type=int, default=5)
     p.add_argument("--probe-alpha", type=float, default=None, help="--probe descriptor: alpha (default 0.01)")
+    p.add_argument("--probe-beta", type=float, default=None, help="--probe descriptor: beta (default 0.01)")
     p.add_argument("--probe-pull-probe", type=int, default=0, help="--probe descriptor: pull_probe")
     p.add_argument("--probe-batch", type=int, default=None, metavar="S",
                    help="profiling aid: the workload's first S sources as one batch with the autotuned batch "
@@ -102,6 +103,8 @@ def run_probe(args):
     kw = {"pull_probe": args.probe_pull_probe}
     if args.probe_alpha is not None:
         kw["alpha"] = args.probe_alpha
+    if args.probe_beta is not None:
+        kw["beta"] = args.probe_beta
     for _ in range(args.repeat):
         gbx.bfs(g, s, depth, parent, gbx.desc_init(**kw))
     listed = srcs if args.probe < 0 else [s]
@@ -764,22 +767,42 @@ def batched_measurements(g, n, sources, reached, single_value, args):
     import synth
     from paper_1804_03327_gb300 import gbx
 
-    def time_batch(gg, srcs, nn, reps=3, tune_srcs=None):
-        # batch descriptor autotuned on other seeded sources of the same graph and width
-        bdesc, _ = gbx.autotune(gg, gbx.TUNE_BATCH, tune_srcs if tune_srcs is not None else srcs)
-        depth = torch.empty((len(srcs), nn), dtype=torch.int16, device="cuda")
-        gbx.bfs_batch(gg, srcs, depth, bdesc)
-        gbx.graph_sync(gg)
+    def time_batch(gg, srcs, nn, reps=3, tune_srcs=None, dtype=torch.int32, bdesc=None, with_int16=True):
+        # batch descriptor autotuned on other seeded sources of the same graph and width (or given);
+        # int32 depth rows, as the single-source runs write (int16 rows timed beside them)
+        if bdesc is None:
+            bdesc, _ = gbx.autotune(gg, gbx.TUNE_BATCH, tune_srcs if tune_srcs is not None else srcs)
+        out = {}
+        for dt in ((dtype, torch.int16) if with_int16 else (dtype,)):
+            depth = torch.empty((len(srcs), nn), dtype=dt, device="cuda")
+            gbx.bfs_batch(gg, srcs, depth, bdesc)
+            gbx.graph_sync(gg)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                gbx.bfs_batch(gg, srcs, depth, bdesc)
+            e1.record()
+            torch.cuda.synchronize()
+            gbx.graph_sync(gg)
+            del depth
+            out[dt] = e0.elapsed_time(e1) / reps / 1e3
+        tuned = {k: gbx.desc_dict(bdesc)[k] for k in ("alpha", "pull_probe", "blocks_per_sm")}
+        return out[dtype], tuned, out.get(torch.int16), bdesc
+
+    def time_single(gg, srcs, nn, tune_srcs):
+        # the same sources one at a time through gbx_bfs, with its own autotuned descriptor
+        sdesc, _ = gbx.autotune(gg, gbx.TUNE_BFS, tune_srcs)
+        d = torch.empty(nn, dtype=torch.int32, device="cuda")
+        gbx.bfs(gg, int(srcs[0]), d, None, sdesc)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        for _ in range(reps):
-            gbx.bfs_batch(gg, srcs, depth, bdesc)
+        for s0 in srcs:
+            gbx.bfs(gg, int(s0), d, None, sdesc)
         e1.record()
         torch.cuda.synchronize()
         gbx.graph_sync(gg)
-        del depth
-        tuned = {k: gbx.desc_dict(bdesc)[k] for k in ("alpha", "pull_probe", "blocks_per_sm")}
-        return e0.elapsed_time(e1) / reps / 1e3, tuned
+        tuned = {k: gbx.desc_dict(sdesc)[k] for k in ("heuristic", "alpha", "beta", "pull_probe", "blocks_per_sm")}
+        return e0.elapsed_time(e1) / 1e3 / len(srcs), tuned
 
     def reached_of(gg, srcs, nn):
         # reached undirected edges per source, from one traced single-source BFS each
@@ -793,41 +816,49 @@ def batched_measurements(g, n, sources, reached, single_value, args):
 
     res = {}
     import synth as _synth
-    t, tuned = time_batch(g, sources, n, tune_srcs=_synth.sources(n, *args._edges, len(sources), seed=SEED + 200))
+    t, tuned, t16, _ = time_batch(g, sources, n,
+                                  tune_srcs=_synth.sources(n, *args._edges, len(sources), seed=SEED + 200))
     v = sum(reached) / t / 1e9
     import oracle
     og_main = oracle_graph(n, *args._edges)
     res["same_sources_as_one_batch"] = {"workload": WORKLOAD, "S": len(sources), "ms": t * 1e3, "value": v,
-                                        "unit": UNIT, "vs_single_source": v / single_value, "descriptor": tuned,
+                                        "unit": UNIT, "depth": "int32",
+                                        "value_int16_depth": sum(reached) / t16 / 1e9,
+                                        "vs_single_source": v / single_value,
+                                        "single_source": "the headline value (same sources, its autotuned descriptor)",
+                                        "descriptor": tuned,
                                         "cpu_baseline": cpu_parallel_oracle([(og_main, sources, reached)])}
     cfg4 = []
     for name, gen in [("rmat21-ef16", lambda: synth.rmat_edges(21, EDGE_FACTOR, seed=SEED)),
                       ("grid2048-del1pct", lambda: synth.grid_edges(2048, 2048, 0.01, seed=SEED))]:
         nn, ss, dd = gen()
         gg = gbx.graph_build(nn, ss, dd)
-        widths = (64, 256, 1024) if name.startswith("rmat") else (64,)
+        widths = (64, 256, 1024)
+        grid = name.startswith("grid")
         all_src = synth.sources(nn, ss, dd, max(widths), seed=SEED)
         tune_all = synth.sources(nn, ss, dd, max(widths), seed=SEED + 300)
-        # single-source reference on the first 64 of these sources
-        d = torch.empty(nn, dtype=torch.int32, device="cuda")
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        gbx.bfs(gg, int(all_src[0]), d, None)
-        e0.record()
-        for s0 in all_src[:64]:
-            gbx.bfs(gg, int(s0), d, None)
-        e1.record()
-        torch.cuda.synchronize()
-        single_s = e0.elapsed_time(e1) / 1e3 / 64
+        # single-source reference on 64 of these sources (16 on the grid, whose BFS runs thousands
+        # of levels), autotuned on other sources (4 on the grid)
+        n_single = 16 if grid else 64
+        single_s, single_desc = time_single(gg, all_src[:n_single], nn, tune_all[:4 if grid else 16])
         reach = reached_of(gg, all_src, nn)
         import oracle
         cpu_b = cpu_parallel_oracle([(oracle_graph(nn, ss, dd), all_src[:64], reach[:64])])
+        gdesc = None
         for S in widths:
-            tb, tuned = time_batch(gg, all_src[:S], nn, reps=1 if name.startswith("grid") else 3,
-                                   tune_srcs=tune_all[:S])
+            # the grid's wide batches (seconds each) reuse the descriptor tuned at S = 64
+            tb, tuned, tb16, bd = time_batch(gg, all_src[:S], nn, reps=1 if grid else 3, tune_srcs=tune_all[:S],
+                                             bdesc=gdesc, with_int16=not grid)
+            if grid:
+                gdesc = bd
             edges = sum(reach[:S])
             cfg4.append({"graph": name, "S": S, "ms": tb * 1e3, "value": edges / tb / 1e9, "unit": UNIT,
+                         "depth": "int32", "value_int16_depth": edges / tb16 / 1e9 if tb16 else None,
+                         "descriptor_tuned_at_S": 64 if grid else S,
                          "single_source_value": edges / (single_s * S) / 1e9,
-                         "speedup_vs_single_source": single_s * S / tb, "descriptor": tuned, "cpu_baseline": cpu_b})
+                         "speedup_vs_single_source": single_s * S / tb, "descriptor": tuned,
+                         "single_source_descriptor": single_desc, "single_source_sample": n_single,
+                         "cpu_baseline": cpu_b})
         gg.free()
     res["configs"] = cfg4
     return res
@@ -934,6 +965,77 @@ def served_measurement(main_graph, args):
     sustainable = run(max(1.0, 0.5 * saturated["throughput_qps"]), SEED + 1)
     st = srv.stats()
     srv.destroy()
+
+    # The same query streams answered one query at a time through gbx_bfs (each graph with
+    # its own autotuned single-source descriptor), on one stream: the per-source form.
+    stream = torch.cuda.Stream()
+    inflight_cap = 32
+    for gi in graphs:
+        src_e, dst_e = gi["edges"]
+        grid = gi["name"].startswith("grid")
+        tune = synth.sources(gi["n"], src_e, dst_e, 2 if grid else 8, seed=SEED + 500)
+        gi["sdesc"], _ = gbx.autotune(gi["g"], gbx.TUNE_BFS, tune)
+        gi["srows"] = torch.empty((inflight_cap, gi["n"]), dtype=torch.int32, device="cuda")
+
+    def run_single(rate, seed):
+        rng = np.random.default_rng(seed)  # the stream run(rate, seed) served
+        warm, span = 0.5, args.serve_seconds
+        t_arr = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * (warm + span) * 1.3) + 16))
+        t_arr = t_arr[t_arr < warm + span]
+        which = rng.integers(0, len(graphs), size=len(t_arr))
+        pick = rng.integers(0, 256, size=len(t_arr))
+        pending = []  # (event, query index) in stream order
+        lat, edges_done, done_n, issued = [], 0, 0, 0
+        # a saturated per-source form never catches up with the arrivals: its throughput is the
+        # completions seen inside the window [warm, warm + span), whatever their arrival time
+        t0 = time.perf_counter()
+        i = 0
+        while True:
+            now = time.perf_counter() - t0
+            # queries arriving after the window are not taken (a backlog the per-source form never clears)
+            while i < len(t_arr) and t_arr[i] <= now and len(pending) < inflight_cap:
+                gi = graphs[which[i]]
+                s0 = int(gi["cand"][pick[i]])
+                with torch.cuda.stream(stream):
+                    gbx.bfs(gi["g"], s0, gi["srows"][i % inflight_cap], None, gi["sdesc"], stream=stream)
+                    ev = torch.cuda.Event()
+                    ev.record(stream)
+                pending.append((ev, i))
+                issued += 1
+                i += 1
+            while pending and pending[0][0].query():
+                ev, q = pending.pop(0)
+                t_seen = time.perf_counter() - t0
+                done_n += 1
+                if warm <= t_seen < warm + span:
+                    gi = graphs[which[q]]
+                    lat.append(t_seen - t_arr[q])
+                    edges_done += gi["reach"].get(int(gi["cand"][pick[q]]), 0)
+            if now > warm + span:
+                if not pending:
+                    break
+                if i < len(t_arr):
+                    i = len(t_arr)  # stop taking queries; drain what was issued
+        for gi in graphs:
+            gbx.graph_sync(gi["g"])
+        lat = np.array(lat) if lat else np.array([0.0])
+        window = span
+        return {"arrival_rate_qps": rate, "arrivals": int(len(t_arr)), "issued": issued,
+                "measured_queries": int(len(lat)), "completed": done_n,
+                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "value": edges_done / window / 1e9, "unit": UNIT, "throughput_qps": len(lat) / window}
+
+    single_sat = run_single(args.serve_rate, SEED)
+    single_half = run_single(max(1.0, 0.5 * single_sat["throughput_qps"]), SEED + 1)
+    per_source = {"at_configured_rate": single_sat, "at_half_saturated_throughput": single_half,
+                  "descriptor_per_graph": {gi["name"]: {k: gbx.desc_dict(gi["sdesc"])[k]
+                                                        for k in ("heuristic", "alpha", "beta", "pull_probe")}
+                                           for gi in graphs},
+                  "note": "one query at a time on one stream (gbx_bfs, int32 depth), at most 32 issued ahead; "
+                          "throughput and latency over the queries completing inside the 2 s window after "
+                          "warm-up (arrival -> completion seen); arrivals never issued are not counted"}
+    for gi in graphs:
+        del gi["srows"]
     for gi in graphs:
         if gi["own"]:
             gi["g"].free()
@@ -948,6 +1050,8 @@ def served_measurement(main_graph, args):
     return {"graphs": [gi["name"] for gi in graphs], "at_configured_rate": saturated,
             "cpu_baseline": cpu_s,
             "at_half_saturated_throughput": sustainable,
+            "per_source_same_mix": per_source,
+            "served_vs_per_source_saturated_gteps": saturated["value"] / max(single_sat["value"], 1e-12),
             "mean_reached_edges_per_query": mean_edges,
             "gteps_needed_for_configured_rate": args.serve_rate * mean_edges / 1e9,
             "server": {"slots": slots, "max_batch": 64, "depth": "int16", "scratch_bytes": st["scratch_bytes"],
