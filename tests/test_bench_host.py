@@ -46,8 +46,8 @@ def test_committed_dram_summary_is_well_formed():
             k, v = line.split("=", 1)
             kv[k.strip()] = v.strip()
     assert len(kv["kernel_source_sha"]) == 16 and int(kv["kernel_source_sha"], 16) >= 0
-    # DRAM moves whole sectors: at least the algorithmic bytes of the captured launch
-    assert float(kv["dram_bytes_per_launch"]) >= float(kv["algorithmic_bytes_of_captured_launch"])
+    # DRAM moves whole sectors: at least the algorithmic bytes per launch of the same sources
+    assert float(kv["dram_bytes_per_launch"]) >= float(kv["algorithmic_bytes_per_launch_64_sources"])
 
 
 def test_traffic_only_for_the_profiled_source(tmp_path, monkeypatch):
