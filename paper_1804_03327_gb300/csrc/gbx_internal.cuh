@@ -129,7 +129,8 @@ struct Graph {
     int32_t* in_col = nullptr;
     uint32_t* nz_in = nullptr;   // bit v set iff in-degree(v) > 0
     uint32_t* nz_out = nullptr;  // bit v set iff out-degree(v) > 0
-    uint32_t* multi_in = nullptr;  // bit v set iff in-degree(v) > 1
+    uint32_t* multi_in = nullptr;   // bit v set iff in-degree(v) > 1
+    uint32_t* multi_out = nullptr;  // bit v set iff out-degree(v) > 1 (aliases multi_in when symmetric)
     // first (smallest) in-neighbour of each row, -1 if none: the first probe of a
     // pull row reads this dense array instead of a random sector of in_col
     int32_t* first_in = nullptr;
@@ -322,7 +323,8 @@ struct MxvStats {
 
 __global__ void __launch_bounds__(kMxvThreads)
     mxv_pull_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col, const int32_t* __restrict__ first,
-                    const uint32_t* __restrict__ nzrows, const uint32_t* __restrict__ ubm,
+                    const uint32_t* __restrict__ nzrows, const uint32_t* __restrict__ multi,
+                    const uint32_t* __restrict__ ubm,
                     const uint32_t* __restrict__ pass, uint32_t* __restrict__ R, int32_t nwords, int early_exit,
                     const int32_t* flag, MxvStats* stats, int32_t* huge, int32_t* huge_next, int32_t* huge_count);
 

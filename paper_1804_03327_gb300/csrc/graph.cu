@@ -179,6 +179,7 @@ static void graph_release(Graph* g) {
     f(g->out_ptr);
     f(g->out_col);
     f(g->nz_in);
+    if (g->multi_out != g->multi_in) f(g->multi_out);
     f(g->multi_in);
     if (g->nz_out != g->nz_in) f(g->nz_out);
     if (g->first_out != g->first_in) f(g->first_out);
@@ -308,7 +309,10 @@ static gbx_status build_impl(Graph* g, int32_t n, int64_t m, const int32_t* src,
     nonzero_rows_kernel<<<div_up(nw32, 256), 256, 0, s>>>(g->in_ptr, n, 2, g->multi_in);
     if (sym) {
         g->nz_out = g->nz_in;
+        g->multi_out = g->multi_in;
     } else {
+        GBX_CUDA_TRY(cudaMalloc((void**)&g->multi_out, sizeof(uint32_t) * ((size_t)g->nwords + 1)));
+        nonzero_rows_kernel<<<div_up(nw32, 256), 256, 0, s>>>(g->out_ptr, n, 2, g->multi_out);
         GBX_CUDA_TRY(cudaMalloc((void**)&g->nz_out, sizeof(uint32_t) * ((size_t)g->nwords + 1)));
         nonzero_rows_kernel<<<div_up(nw32, 256), 256, 0, s>>>(g->out_ptr, n, 1, g->nz_out);
     }

@@ -35,10 +35,12 @@ __device__ __forceinline__ bool dir_enabled(const int32_t* flag, int want) { ret
 // finished by the whole warp 32 entries at a time.  With early exit a row stops
 // at its first hit (Section 5.3); the result is the same either way.
 constexpr int kMxvIlp = 2;
+constexpr int kMxvP1 = 4;  // first-pass rows per lane per round
 
 __global__ void __launch_bounds__(kMxvThreads) mxv_pull_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
                                                                 const int32_t* __restrict__ first,
                                                                 const uint32_t* __restrict__ nzrows,
+                                                                const uint32_t* __restrict__ multi,
                                                                 const uint32_t* __restrict__ ubm,
                                                                 const uint32_t* __restrict__ pass, uint32_t* __restrict__ R,
                                                                 int32_t nwords, int early_exit, const int32_t* flag,
@@ -55,16 +57,56 @@ __global__ void __launch_bounds__(kMxvThreads) mxv_pull_kernel(const int32_t* __
     for (int32_t tile = gwarp; tile < ntiles; tile += nwarps) {
         const int32_t w = (tile << 5) + lane;
         const bool wok = w < nwords;
-        const uint32_t cand = wok ? ((pass ? pass[w] : 0xffffffffu) & nzrows[w]) : 0u;
+        const uint32_t cand0 = wok ? ((pass ? pass[w] : 0xffffffffu) & nzrows[w]) : 0u;
+        hits[lane] = 0u;
+        __syncwarp();
+        // a tile with more candidates than one round first tests every candidate's first entry
+        // (the dense first-entry array: no row offsets loaded); the rest goes on with the rows it
+        // left open that have more entries
+        const uint32_t cnt0 = __popc(cand0);
+        const uint32_t incl0 = warp_inclusive_sum(cnt0);
+        const uint32_t total0 = __shfl_sync(0xffffffffu, incl0, 31);
+        const bool two_pass = first != nullptr && total0 > 32u * kMxvIlp;
+        if (two_pass) {
+            const uint32_t excl0 = incl0 - cnt0;
+            for (uint32_t base = 0; base < total0; base += 32 * kMxvP1) {
+                int32_t i[kMxvP1], f0[kMxvP1];
+#pragma unroll
+                for (int r = 0; r < kMxvP1; ++r) {
+                    const uint32_t c = base + 32 * r + lane;
+                    int j = 0;
+#pragma unroll
+                    for (int step = 16; step >= 1; step >>= 1) {
+                        const uint32_t ev = __shfl_sync(0xffffffffu, excl0, j + step);
+                        if (ev <= c) j += step;
+                    }
+                    const uint32_t cj = __shfl_sync(0xffffffffu, cand0, j);
+                    const uint32_t ej = __shfl_sync(0xffffffffu, excl0, j);
+                    i[r] = c < total0 ? (((tile << 5) + j) << 5) + (int)__fns(cj, 0u, (int)(c - ej) + 1) : -1;
+                }
+#pragma unroll
+                for (int r = 0; r < kMxvP1; ++r) f0[r] = i[r] >= 0 ? first[i[r]] : -1;
+#pragma unroll
+                for (int r = 0; r < kMxvP1; ++r) {
+                    if (i[r] < 0) continue;
+                    rows += 1;
+                    exam += 1;
+                    if (bit_test(ubm, f0[r])) atomicOr(hits + ((i[r] >> 5) - (tile << 5)), 1u << (i[r] & 31));
+                }
+            }
+            __syncwarp();
+        }
+        const uint32_t f1 = hits[lane];  // rows the first pass found
+        const uint32_t cand =
+            two_pass ? cand0 & (multi ? (wok ? multi[w] : 0u) : 0xffffffffu) & (early_exit ? ~f1 : 0xffffffffu) : cand0;
         const uint32_t cntw = __popc(cand);
         const uint32_t incl = warp_inclusive_sum(cntw);
         const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
         const uint32_t excl = incl - cntw;
-        hits[lane] = 0u;
-        __syncwarp();
         for (uint32_t base = 0; base < total; base += 32 * kMxvIlp) {
             bool mine[kMxvIlp], found[kMxvIlp], done[kMxvIlp];
             int jw[kMxvIlp], bitpos[kMxvIlp];
+            uint32_t f1w[kMxvIlp];
             int32_t k[kMxvIlp], end[kMxvIlp], beg[kMxvIlp], f0[kMxvIlp];
 #pragma unroll
             for (int r = 0; r < kMxvIlp; ++r) {
@@ -79,6 +121,7 @@ __global__ void __launch_bounds__(kMxvThreads) mxv_pull_kernel(const int32_t* __
                 jw[r] = j;
                 const uint32_t cj = __shfl_sync(0xffffffffu, cand, j);
                 const uint32_t ej = __shfl_sync(0xffffffffu, excl, j);
+                f1w[r] = __shfl_sync(0xffffffffu, f1, j);
                 bitpos[r] = mine[r] ? (int)__fns(cj, 0u, (int)(c - ej) + 1) : 0;
                 found[r] = false;
                 done[r] = false;
@@ -88,14 +131,18 @@ __global__ void __launch_bounds__(kMxvThreads) mxv_pull_kernel(const int32_t* __
                 const int32_t i = (((tile << 5) + jw[r]) << 5) + bitpos[r];
                 beg[r] = mine[r] ? ptr[i] : 0;
                 end[r] = mine[r] ? ptr[i + 1] : 0;
-                f0[r] = mine[r] ? (first ? first[i] : -2) : -1;
+                f0[r] = (mine[r] && !two_pass) ? (first ? first[i] : -2) : -1;
             }
 #pragma unroll
             for (int r = 0; r < kMxvIlp; ++r) {
                 if (!mine[r]) continue;
+                k[r] = beg[r] + 1;
+                if (two_pass) {  // the first entry was examined (and counted) by the first pass
+                    found[r] = (f1w[r] >> bitpos[r]) & 1u;  // only without early exit can it be set here
+                    continue;
+                }
                 rows += 1;
                 if (f0[r] == -2) f0[r] = col[beg[r]];  // no first-entry array: read the row's first entry
-                k[r] = beg[r] + 1;
                 exam += 1;
                 if (bit_test(ubm, f0[r])) {
                     found[r] = true;
@@ -529,7 +576,8 @@ gbx_status mxv_issue(Graph* G, gbx_vector* w, const gbx_vector* mask, int32_t se
             int32_t* huge_next = G->ws.qp[1];
             int32_t* huge_count = G->ws.flag + 2;
             GBX_CUDA_TRY(cudaMemsetAsync(huge_count, 0, sizeof(int32_t), s));
-            mxv_pull_kernel<<<G->num_sms * 8, kMxvThreads, 0, s>>>(pull_ptr, pull_col, pull_first, pull_nz, ubm,
+            mxv_pull_kernel<<<G->num_sms * 8, kMxvThreads, 0, s>>>(pull_ptr, pull_col, pull_first, pull_nz,
+                                                                    d.transpose ? G->multi_in : G->multi_out, ubm,
                                                                     pass_bm, R, G->nwords, d.early_exit ? 1 : 0, flag,
                                                                     stats, huge, huge_next, huge_count);
             mxv_pull_huge_kernel<<<G->num_sms * 8, kMxvThreads, 0, s>>>(pull_ptr, pull_col, ubm, R, huge, huge_next,
