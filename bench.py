@@ -639,15 +639,21 @@ def sssp_bytes(tr, n: int) -> int:
     """Algorithmic bytes of one SSSP from its iteration trace: push iterations read
     12 B per queued vertex (id, prefix, row start), 12 B per relaxed edge (column,
     weight, distance of the target) and write 16 B per improved vertex (distance,
-    stamp, queue slot and prefix); pull iterations read every row's two offsets
-    (8 B) plus 12 B per in-edge and write the n/8-byte improved-set bitmap and the
-    improved distances; the initialisation writes distances and stamps (8n)."""
+    stamp, queue slot and prefix); pull iterations read the list of rows with
+    in-edges and where their in-edges start (at most 8 B a vertex) plus 12 B per
+    in-edge (column, weight, source distance) and write 8 B per improved vertex
+    (distance, stamp); a pull followed by a push reads the n stamps once to
+    queue the improved vertices; the initialisation writes distances and stamps
+    (8n)."""
     total = 8 * n
-    for r in tr:
-        if r["direction"] == 1:  # push
+    dirs = [int(r["direction"]) for r in tr]
+    for i, r in enumerate(tr):
+        if dirs[i] == 1:  # push
             total += 12 * int(r["nf"]) + 12 * int(r["e_exam"]) + 16 * int(r["n_new"])
         else:
-            total += 8 * n + 12 * int(r["e_exam"]) + n // 8 + 4 * int(r["n_new"])
+            total += 8 * n + 12 * int(r["e_exam"]) + 8 * int(r["n_new"])
+            if i + 1 < len(dirs) and dirs[i + 1] == 1:
+                total += 4 * n
     return total
 
 

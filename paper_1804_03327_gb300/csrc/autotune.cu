@@ -112,9 +112,10 @@ extern "C" gbx_status gbx_autotune(gbx_graph* g, int32_t kind, const int32_t* so
         }
     } else {
         // SSSP: the switch rule on the improved-set size (beta = 0 keeps the two
-        // phases of Section 5.6), push only and pull only
+        // phases of Section 5.6; a large beta returns to push as soon as the
+        // improved set shrinks), push only and pull only
         const float alphas[] = {0.002f, 0.01f, 0.05f, 0.2f};
-        const float betas[] = {0.0f, 0.01f};
+        const float betas[] = {0.0f, 0.01f, 0.1f, 0.3f};
         for (float b : betas)
             for (float a : alphas) {
                 gbx_desc d = base;

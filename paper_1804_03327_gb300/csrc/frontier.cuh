@@ -271,12 +271,10 @@ struct PushCursorT {
     int32_t wlast;
     int32_t wv[I];
 
-    // Maps the edges [base, base + kStep) of one step (lane t-th slot: edge
-    // base + 32 t + lane) to their queue entries and loads each edge's frontier
-    // vertex u (-1 at or past e1) and d = (row start - prefix) of its entry, so that
-    // the edge's CSR position is e + d.  The loads are issued, not waited for.
-    __device__ __forceinline__ void map(const int32_t* q, const int32_t* qp, const int32_t* qd, uint32_t qcount,
-                                        int32_t base, int32_t e1, int32_t (&u)[I], int32_t (&d)[I]) {
+    // Occupancy of the step [base, base + kStep) by entry boundaries: bit j of
+    // occ[m] is set iff an entry after the cursor's starts at edge base + 32 m + j
+    // (the window is reloaded first if the step could reach past it).
+    __device__ __forceinline__ void occupancy(const int32_t* qp, uint32_t qcount, int32_t base, uint32_t (&occ)[I]) {
         const int lane = threadIdx.x & 31;
         if (wlast <= base + kStep - 1) {
 #pragma unroll
@@ -286,8 +284,6 @@ struct PushCursorT {
             }
             wlast = __shfl_sync(0xffffffffu, wv[I - 1], 31);
         }
-        // occupancy of [base, base + kStep) by boundaries, one 32-bit word per lane-edge slot
-        uint32_t occ[I];
 #pragma unroll
         for (int m = 0; m < I; ++m) {
             uint32_t c = 0;
@@ -298,6 +294,17 @@ struct PushCursorT {
             }
             occ[m] = __reduce_or_sync(0xffffffffu, c);
         }
+    }
+
+    // Maps the edges [base, base + kStep) of one step (lane t-th slot: edge
+    // base + 32 t + lane) to their queue entries and loads each edge's frontier
+    // vertex u (-1 at or past e1) and d = (row start - prefix) of its entry, so that
+    // the edge's CSR position is e + d.  The loads are issued, not waited for.
+    __device__ __forceinline__ void map(const int32_t* q, const int32_t* qp, const int32_t* qd, uint32_t qcount,
+                                        int32_t base, int32_t e1, int32_t (&u)[I], int32_t (&d)[I]) {
+        const int lane = threadIdx.x & 31;
+        uint32_t occ[I];
+        occupancy(qp, qcount, base, occ);
         uint32_t before = 0;
 #pragma unroll
         for (int t = 0; t < I; ++t) {
@@ -310,6 +317,23 @@ struct PushCursorT {
                 u[t] = q[kk];
                 d[t] = qd[kk];
             }
+        }
+        k += (int32_t)before;
+    }
+
+    // The entry of each lane's edge slots of the step [base, base + kStep) (qp must
+    // be strictly ascending: no entry without edges); the cursor moves on to the
+    // entry of the step's last edge.  A slot at or past the end of the last entry's
+    // edges maps to the last entry.
+    __device__ __forceinline__ void locate(const int32_t* qp, uint32_t qcount, int32_t base, int32_t (&kk)[I]) {
+        const int lane = threadIdx.x & 31;
+        uint32_t occ[I];
+        occupancy(qp, qcount, base, occ);
+        uint32_t before = 0;
+#pragma unroll
+        for (int t = 0; t < I; ++t) {
+            kk[t] = k + (int32_t)(before + __popc(occ[t] & (0xffffffffu >> (31 - lane))));
+            before += __popc(occ[t]);
         }
         k += (int32_t)before;
     }

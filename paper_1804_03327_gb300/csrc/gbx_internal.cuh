@@ -139,6 +139,12 @@ struct Graph {
     // in_val[k] to in_col[k] (aliases out_val when symmetric); NULL until set
     float* out_val = nullptr;
     float* in_val = nullptr;
+    // the rows with in-edges, ascending (nzr_in), and where their in-edges start
+    // (nzr_in_ptr, nnzr_in + 1 entries, the last = nnz): the edge-balanced (min, +)
+    // pull walks these.  One allocation, made with the weights.
+    int32_t* nzr_in = nullptr;
+    int32_t* nzr_in_ptr = nullptr;
+    int32_t nnzr_in = 0;
     int32_t drop_self_loops = 0;  // as built
     Workspace ws;  // scratch of the operations called on this graph (ordered on one stream)
     // host-side copies for gbx_bfs_host (allocated on first use)

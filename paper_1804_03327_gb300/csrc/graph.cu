@@ -186,6 +186,7 @@ static void graph_release(Graph* g) {
     f(g->first_in);
     if (g->in_val != g->out_val) f(g->in_val);
     f(g->out_val);
+    f(g->nzr_in);
     workspace_release(g->ws);
     for (int i = 0; i < 2; ++i) {
         f(g->hdepth[i]);

@@ -18,11 +18,11 @@ namespace gbx {
 
 constexpr int kSsspThreads = 512;
 // Register budgets: the default build fits two 512-thread blocks on an SM (64
-// registers, no spills), the lean build three (40 registers, ~200 bytes of spills).
-// Lean hides more gather latency on push iterations over a skewed graph (RMAT-22
-// push only: 2.61 -> 2.28 ms) and loses where pull iterations or many small ones
-// dominate (the direction rule on RMAT-22 3.27 -> 4.89 ms, a 1024x1024 grid +16 %),
-// so a descriptor chooses it (blocks_per_sm >= 3) and the autotuner times it.
+// registers), the lean build three (40 registers, ~230 bytes of spills).  Lean
+// once hid gather latency on push iterations that waited on one load at a time;
+// with the pipelined push and the edge-balanced pull it spills on the hot loops
+// and loses (RMAT-22 push only 1.70 -> 3.38 ms, pull only 4.09 -> 4.62 ms), but a
+// descriptor can still choose it (blocks_per_sm >= 3) and the autotuner times it.
 constexpr int kSsspOcc = 2;
 constexpr int kSsspOccLean = 3;
 
@@ -34,10 +34,11 @@ struct SsspArgs {
     const int32_t* in_ptr;
     const int32_t* in_col;
     const float* in_val;
-    const uint32_t* nz_in;
+    const int32_t* nzr;      // rows with in-edges, ascending
+    const int32_t* nzr_ptr;  // their first in-edge (nnzr + 1 entries)
+    int32_t nnzr, nnz;
     float* dist;
-    int32_t* stamp;  // iteration + 1 at which the vertex was last queued (dedup of the push queue)
-    uint32_t* chg;   // pull: bit v = dist[v] improved in this iteration
+    int32_t* stamp;  // iteration + 1 at which the vertex last improved (dedup of the push queue)
     int32_t* q[2];
     int32_t* qp[2];
     int32_t* qd[2];
@@ -52,9 +53,17 @@ struct SsspArgs {
 };
 
 // Push: relax the out-edges of the queued vertices, edge-balanced over warps.
-// A vertex whose distance drops is queued once for the next iteration.
+// A vertex whose distance drops is queued once for the next iteration.  A warp
+// range of more than one step is walked as a software pipeline of five stages,
+// each on a different step of 32 edges: (1) map the edges to queue entries and
+// load their vertex u and row offset, (2) load the child v, the weight and d[u],
+// (3) load d[v], (4) lower d[v] with an atomic minimum where d[u] + w is below
+// it, (5) claim the lowered children for the next queue (atomicMax on stamp).
+// One iteration issues the memory operations of all five stages before it waits
+// for any of them.
 __device__ __forceinline__ void sssp_push(const SsspArgs& a, int32_t L, int cur, uint32_t qcount, uint32_t qedges,
                                           Stage& stg, Acc& acc) {
+    const int lane = threadIdx.x & 31;
     const int gwarp = (int)((blockIdx.x * kSsspThreads + threadIdx.x) >> 5);
     const int nwarps = (int)((gridDim.x * kSsspThreads) >> 5);
     const int32_t* q = a.q[cur];
@@ -62,96 +71,279 @@ __device__ __forceinline__ void sssp_push(const SsspArgs& a, int32_t L, int cur,
     const int32_t* qd = a.qd[cur];
     const int32_t E = (int32_t)qedges;
     int32_t chunk = (int32_t)(((long long)E + nwarps - 1) / nwarps);
-    chunk = chunk < kPushStep ? kPushStep : ((chunk + kPushStep - 1) / kPushStep) * kPushStep;
+    chunk = chunk < 32 ? 32 : ((chunk + 31) / 32) * 32;
     for (long long e0l = (long long)gwarp * chunk; e0l < E; e0l += (long long)nwarps * chunk) {
         const int32_t e0 = (int32_t)e0l;
         const int32_t e1 = E - e0 > chunk ? e0 + chunk : E;
-        PushCursor cur_;
+        const int32_t nsteps = (e1 - e0 + 31) / 32;
+        PushCursorT<1> cur_;
         cur_.k = warp_find_entry(qp, (int32_t)qcount, e0);
         cur_.wlast = -1;
-        for (int32_t base = e0; base < e1; base += kPushStep) {
-            const PushStep st = cur_.gather(a.out_col, q, qp, qd, qcount, base, e1);
-            bool queued[kPushIlp];
-#pragma unroll
-            for (int t = 0; t < kPushIlp; ++t) {
-                queued[t] = false;
-                if (st.u[t] < 0) continue;
-                const float x = a.dist[st.u[t]] + __ldg(a.out_val + st.k[t]);
-                if (x < a.dist[st.v[t]]) {
-                    const float old = atomic_min_f32(a.dist + st.v[t], x);
-                    if (x < old) queued[t] = atomicMax(a.stamp + st.v[t], L + 1) < L + 1;
+        if (nsteps == 1) {
+            // a single step (a small queue): no pipeline fill and drain
+            const PushStepT<1> st = cur_.gather(a.out_col, q, qp, qd, qcount, e0, e1);
+            bool queued = false;
+            if (st.u[0] >= 0) {
+                const float x = a.dist[st.u[0]] + __ldg(a.out_val + st.k[0]);
+                if (x < a.dist[st.v[0]]) {
+                    const float old = atomic_min_f32(a.dist + st.v[0], x);
+                    if (x < old) queued = atomicMax(a.stamp + st.v[0], L + 1) < L + 1;
                 }
             }
-#pragma unroll
-            for (int t = 0; t < kPushIlp; ++t) {
-                acc.exam += st.u[t] >= 0 ? 1u : 0u;
-                if (queued[t]) acc.n_new += 1;
-                stg.put(queued[t], st.v[t]);
+            acc.exam += st.u[0] >= 0 ? 1u : 0u;
+            if (queued) acc.n_new += 1;
+            stg.put(queued, st.v[0]);
+            continue;
+        }
+        // stage registers (a child < 0 marks an empty slot: past e1, pipeline fill or drain)
+        int32_t u1 = -1, d1 = 0;               // after stage 1: vertex, row start - prefix
+        int32_t v2 = -1;                       // after stage 2: child, weight, d[u]
+        float w2 = 0.0f, du2 = 0.0f;
+        int32_t v3 = -1;                       // after stage 3: child, candidate, d[v]
+        float x3 = 0.0f, dv3 = 0.0f;
+        int32_t v4 = -1;                       // after stage 4: child, candidate, d[v] before the minimum
+        float x4 = 0.0f, old4 = 0.0f;
+        for (int32_t it = 0; it < nsteps + 4; ++it) {
+            // stage 5 (step it - 4): claim the children whose distance the candidate lowered
+            const bool lowered = v4 >= 0 && x4 < old4;
+            const int32_t prev = lowered ? atomicMax(a.stamp + v4, L + 1) : L + 1;
+            // stage 4 (step it - 3): lower d[v] where the candidate is below the d[v] read
+            const float old3 = v3 >= 0 && x3 < dv3 ? atomic_min_f32(a.dist + v3, x3) : x3;
+            // stage 3 (step it - 2): d[v]
+            const float dv2 = v2 >= 0 ? a.dist[v2] : 0.0f;
+            // stage 2 (step it - 1): child, weight, d[u]
+            int32_t v1 = -1;
+            float w1 = 0.0f, du1 = 0.0f;
+            if (u1 >= 0) {
+                const int32_t kpos = e0 + (it - 1) * 32 + lane + d1;
+                v1 = __ldg(a.out_col + kpos);
+                w1 = __ldg(a.out_val + kpos);
+                du1 = a.dist[u1];
             }
+            // stage 1 (step it): queue entries
+            int32_t u0[1] = {-1}, d0[1] = {0};
+            if (it < nsteps) cur_.map(q, qp, qd, qcount, e0 + it * 32, e1, u0, d0);
+            // stage 5, continued: queue the claimed children
+            const bool queued = lowered && prev < L + 1;
+            acc.exam += u1 >= 0 ? 1u : 0u;
+            if (queued) acc.n_new += 1;
+            stg.put(queued, v4);
+            // advance the pipeline
+            v4 = v3;
+            x4 = x3;
+            old4 = old3;
+            v3 = v2;
+            x3 = du2 + w2;
+            dv3 = dv2;
+            v2 = v1;
+            w2 = w1;
+            du2 = du1;
+            u1 = u0[0];
+            d1 = d0[0];
         }
     }
     stg.flush();
 }
 
-// Pull: every row with in-edges takes the minimum over them; a lane per row,
-// rows with more than 32 in-edges reduced by the whole warp.  Improved rows
-// set their bit in chg (one word per warp and tile, written whole).
-__device__ __forceinline__ void sssp_pull(const SsspArgs& a, Acc& acc) {
-    const int lane = threadIdx.x & 31;
-    const int gwarp = (int)((blockIdx.x * kSsspThreads + threadIdx.x) >> 5);
-    const int nwarps = (int)((gridDim.x * kSsspThreads) >> 5);
-    for (int32_t wd = gwarp; wd < a.nwords; wd += nwarps) {
-        const int32_t i = (wd << 5) + lane;
-        const bool has = (a.nz_in[wd] >> lane) & 1u;
-        int32_t beg = 0, end = 0;
-        if (has) {
-            beg = __ldg(a.in_ptr + i);
-            end = __ldg(a.in_ptr + i + 1);
-        }
-        float t = INFINITY;
-        const bool longrow = end - beg > 32;
-        if (!longrow)
-            for (int32_t k = beg; k < end; ++k) t = fminf(t, a.dist[__ldg(a.in_col + k)] + __ldg(a.in_val + k));
-        uint32_t pend = __ballot_sync(0xffffffffu, longrow);
-        while (pend) {
-            const int owner = __ffs(pend) - 1;
-            pend &= pend - 1;
-            const int32_t b = __shfl_sync(0xffffffffu, beg, owner);
-            const int32_t e = __shfl_sync(0xffffffffu, end, owner);
-            float m = INFINITY;
-            for (int32_t k = b + lane; k < e; k += 32) m = fminf(m, a.dist[__ldg(a.in_col + k)] + __ldg(a.in_val + k));
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
-            if (lane == owner) t = m;
-        }
-        bool better = false;
-        if (has && t < a.dist[i]) {
-            a.dist[i] = t;  // this lane owns row i
-            better = true;
-        }
-        const uint32_t word = __ballot_sync(0xffffffffu, better);
-        if (lane == 0) a.chg[wd] = word;
-        acc.exam += (uint32_t)(end - beg);
-        if (better) acc.n_new += 1;
+// Pull: every row with in-edges takes the minimum of d[j] + w(j, i) over them.
+// The in-edges of the rows that have any (the compact list nzr, with nzr_ptr
+// where each row's in-edges start) are cut into equal chunks, one per warp, so a
+// hub row costs no more than its edges.  A warp walks its chunk kSpullStep edges
+// at a time, each lane kSpullVec consecutive edges (one 16-byte load of columns
+// and one of weights, issued a step ahead): the lane takes the minimum over each
+// row's run of its edges, a group minimum over the lanes whose last run belongs
+// to one row joins the rows that cross lanes, and the row still open at the end
+// of a step is carried into the next.  Finished rows are queued in a per-warp
+// ring in shared memory and written 32 at a time, one per lane, so no step waits
+// for the loads of a write.  A row whose in-edges all lie inside the chunk is
+// written by this warp alone; the chunk's first and last row may be shared with
+// the neighbouring chunks and are lowered with an atomic minimum.  An improved
+// row records the iteration in stamp, the set a following push iteration starts
+// from.
+constexpr int kSpullVec = 4;                   // consecutive in-edges per lane and step
+constexpr int kSpullStep = 32 * kSpullVec;     // in-edges per warp and step
+static_assert(kSpullStep == 128, "a step's row starts fit four 32-bit words, one per group of eight lanes");
+// Finished rows wait in a ring of kSpullRing (row entry, minimum) pairs: fewer than
+// 32 are left after a write-out and one step adds at most kSpullStep.
+constexpr int kSpullRing = 256;
+static_assert(kSpullRing >= 31 + kSpullStep && (kSpullRing & (kSpullRing - 1)) == 0, "pull ring size");
+
+struct SpullSmem {
+    uint32_t occ[4];            // row starts of the step, one bit per edge
+    int2 ring[kSpullRing];      // finished rows: (entry, or ~entry when shared; minimum's bits)
+};
+
+// Lowers the distance of row entry kr to m, the row's minimum over this warp's
+// part of its in-edges.  own: no other thread writes that row.
+__device__ __forceinline__ void sssp_pull_commit(const SsspArgs& a, int32_t L, int32_t kr, float m, bool own,
+                                                 Acc& acc) {
+    const int32_t row = __ldg(a.nzr + kr);
+    if (!(m < a.dist[row])) return;  // distances only fall: nothing to lower
+    if (own) {
+        a.dist[row] = m;
+        a.stamp[row] = L + 1;
+        acc.n_new += 1;
+    } else {
+        const float prev = atomic_min_f32(a.dist + row, m);
+        if (m < prev && atomicMax(a.stamp + row, L + 1) < L + 1) acc.n_new += 1;
     }
 }
 
-// The improved set of a pull iteration as the next push queue.
-__device__ __forceinline__ void sssp_chg_to_queue(const SsspArgs& a, Stage& st) {
+// binary32 <-> an unsigned key with the same order (for a warp-wide integer minimum)
+__device__ __forceinline__ uint32_t f32_order_key(float f) {
+    const uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float f32_from_order_key(uint32_t k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// The in-edge columns and weights of a lane's kSpullVec edges from es (none at or past e1).
+__device__ __forceinline__ void sssp_pull_load(const SsspArgs& a, int32_t es, int32_t e1, bool full, int4& c4,
+                                               float4& w4) {
+    if (full) {
+        c4 = __ldcs(reinterpret_cast<const int4*>(a.in_col + es));
+        w4 = __ldcs(reinterpret_cast<const float4*>(a.in_val + es));
+    } else {
+        c4.x = es + 0 < e1 ? __ldcs(a.in_col + es + 0) : 0;
+        c4.y = es + 1 < e1 ? __ldcs(a.in_col + es + 1) : 0;
+        c4.z = es + 2 < e1 ? __ldcs(a.in_col + es + 2) : 0;
+        c4.w = es + 3 < e1 ? __ldcs(a.in_col + es + 3) : 0;
+        w4.x = es + 0 < e1 ? __ldcs(a.in_val + es + 0) : 0.0f;
+        w4.y = es + 1 < e1 ? __ldcs(a.in_val + es + 1) : 0.0f;
+        w4.z = es + 2 < e1 ? __ldcs(a.in_val + es + 2) : 0.0f;
+        w4.w = es + 3 < e1 ? __ldcs(a.in_val + es + 3) : 0.0f;
+    }
+}
+
+// Queues the finished row (entry kr, minimum m) of each lane with `take` (all lanes call).
+__device__ __forceinline__ void sssp_pull_queue(SpullSmem& sm, uint32_t& tail, bool take, int32_t kr, bool own,
+                                                float m) {
+    const uint32_t b = __ballot_sync(0xffffffffu, take);
+    if (take)
+        sm.ring[(tail + __popc(b & lanemask_lt())) & (kSpullRing - 1)] =
+            make_int2(own ? kr : ~kr, __float_as_int(m));
+    tail += __popc(b);
+}
+
+// Writes the queued rows out, 32 at a time, while at least `least` are queued
+// (least = 1: all of them).
+__device__ __forceinline__ void sssp_pull_drain(const SsspArgs& a, int32_t L, SpullSmem& sm, uint32_t& head,
+                                                uint32_t tail, uint32_t least, Acc& acc) {
+    const int lane = threadIdx.x & 31;
+    __syncwarp();
+    while (tail - head >= least) {
+        if ((uint32_t)lane < tail - head) {
+            const int2 e = sm.ring[(head + lane) & (kSpullRing - 1)];
+            sssp_pull_commit(a, L, e.x >= 0 ? e.x : ~e.x, __int_as_float(e.y), e.x >= 0, acc);
+        }
+        head += tail - head < 32u ? tail - head : 32u;
+    }
+    __syncwarp();
+}
+
+// sm: this warp's shared scratch, occ zero on entry and on return.
+__device__ __forceinline__ void sssp_pull(const SsspArgs& a, int32_t L, SpullSmem& sm, Acc& acc) {
     const int lane = threadIdx.x & 31;
     const int gwarp = (int)((blockIdx.x * kSsspThreads + threadIdx.x) >> 5);
     const int nwarps = (int)((gridDim.x * kSsspThreads) >> 5);
-    const int32_t ntiles = (a.nwords + 31) >> 5;
-    for (int32_t tile = gwarp; tile < ntiles; tile += nwarps) {
-        const int32_t wl = (tile << 5) + lane;
-        const uint32_t mine = wl < a.nwords ? a.chg[wl] : 0u;
-        uint32_t todo = __ballot_sync(0xffffffffu, mine != 0u);
-        while (todo) {
-            const int j = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const uint32_t nw = __shfl_sync(0xffffffffu, mine, j);
-            st.put((nw >> lane) & 1u, (((tile << 5) + j) << 5) + lane);
+    const int32_t E = a.nnz;
+    int32_t chunk = (int32_t)(((long long)E + nwarps - 1) / nwarps);
+    chunk = chunk < kSpullStep ? kSpullStep : ((chunk + kSpullStep - 1) / kSpullStep) * kSpullStep;
+    for (long long e0l = (long long)gwarp * chunk; e0l < E; e0l += (long long)nwarps * chunk) {
+        const int32_t e0 = (int32_t)e0l;
+        const int32_t e1 = E - e0 > chunk ? e0 + chunk : E;
+        PushCursorT<kSpullVec> cur_;
+        cur_.k = warp_find_entry(a.nzr_ptr, a.nnzr, e0);
+        cur_.wlast = -1;
+        const int32_t k_first = cur_.k;  // the chunk's first row: may have in-edges before e0
+        int32_t ckey = -1;               // the open row carried from the last step (entry), its minimum
+        float cmin = INFINITY;
+        uint32_t head = 0, tail = 0;     // ring positions (same in every lane)
+        int4 c4;
+        float4 w4;
+        sssp_pull_load(a, e0 + kSpullVec * lane, e1, e1 - e0 >= kSpullStep, c4, w4);
+        for (int32_t base = e0; base < e1; base += kSpullStep) {
+            const int32_t k0 = cur_.k;  // entry of edge base - 1 (of e0 in the first step)
+            const int32_t es = base + kSpullVec * lane;  // this lane's first edge
+            // candidates d[j] + w(j, i) of this step; the next step's edges are loaded meanwhile
+            float x0 = es + 0 < e1 ? a.dist[c4.x] + w4.x : INFINITY;
+            const float x1 = es + 1 < e1 ? a.dist[c4.y] + w4.y : INFINITY;
+            const float x2 = es + 2 < e1 ? a.dist[c4.z] + w4.z : INFINITY;
+            const float x3 = es + 3 < e1 ? a.dist[c4.w] + w4.w : INFINITY;
+            if (base + kSpullStep < e1)
+                sssp_pull_load(a, es + kSpullStep, e1, e1 - base - kSpullStep >= kSpullStep, c4, w4);
+            // row starts in the step: bit j of word m set iff a row starts at edge base + 32 m + j
+            // (none at or past e1, so that slots past e1 stay in the chunk's last row)
+            if (cur_.wlast <= base + kSpullStep - 1) {
+#pragma unroll
+                for (int t = 0; t < kSpullVec; ++t) {
+                    const int32_t wi = cur_.k + 1 + lane + 32 * t;
+                    cur_.wv[t] = wi < a.nnzr ? __ldg(a.nzr_ptr + wi) : INT32_MAX;
+                }
+                cur_.wlast = __shfl_sync(0xffffffffu, cur_.wv[kSpullVec - 1], 31);
+            }
+#pragma unroll
+            for (int t = 0; t < kSpullVec; ++t) {
+                const int32_t rel = cur_.wv[t] - base;  // wv <= INT32_MAX, base >= 0: no overflow
+                if (rel >= 0 && rel < kSpullStep && base + rel < e1) atomicOr(sm.occ + (rel >> 5), 1u << (rel & 31));
+            }
+            __syncwarp();
+            const uint4 o4 = *reinterpret_cast<const uint4*>(sm.occ);
+            __syncwarp();
+            if (lane < 4) sm.occ[lane] = 0u;
+            const uint32_t p0 = __popc(o4.x), p1 = __popc(o4.y), p2 = __popc(o4.z), p3 = __popc(o4.w);
+            cur_.k = k0 + (int32_t)(p0 + p1 + p2 + p3);
+            // this lane's edges es .. es + 3: where rows start among them, the rows before them
+            const int grp = lane >> 3;
+            const int sh = (lane & 7) * kSpullVec;
+            const uint32_t before_grp = grp == 0 ? 0u : (grp == 1 ? p0 : (grp == 2 ? p0 + p1 : p0 + p1 + p2));
+            const uint32_t word = (grp & 2) ? ((grp & 1) ? o4.w : o4.z) : ((grp & 1) ? o4.y : o4.x);
+            const uint32_t bits = (word >> sh) & ((1u << kSpullVec) - 1u);
+            const bool b0 = bits & 1u, b1 = (bits >> 1) & 1u, b2 = (bits >> 2) & 1u, b3 = (bits >> 3) & 1u;
+            const int32_t kk_s = k0 + (int32_t)(before_grp + __popc(word & ((1u << sh) - 1u)) + (b0 ? 1u : 0u));
+            const int32_t kk_e = kk_s + (int32_t)b1 + (int32_t)b2 + (int32_t)b3;  // row of the lane's last edge
+            const int32_t nv = e1 - es;
+            acc.exam += nv <= 0 ? 0u : (nv >= kSpullVec ? (uint32_t)kSpullVec : (uint32_t)nv);
+            // minimum of the run ending at each edge (lane 0 continues the carried row)
+            if (lane == 0 && ckey >= 0 && !b0) x0 = fminf(x0, cmin);
+            const float s0 = x0;
+            const float s1 = b1 ? x1 : fminf(s0, x1);
+            const float s2 = b2 ? x2 : fminf(s1, x2);
+            const float s3 = b3 ? x3 : fminf(s2, x3);
+            // the minimum of each row's open runs over the lanes that end in it (they are adjacent)
+            const uint32_t same = __match_any_sync(0xffffffffu, kk_e);
+            const float gmin = f32_from_order_key(__reduce_min_sync(same, f32_order_key(s3)));
+            float in_min = __shfl_up_sync(0xffffffffu, gmin, 1);
+            if (lane == 0) in_min = cmin;
+            // rows finished here: the row before the lane (it ended at the border), and the rows
+            // ending at edges 0, 1, 2; the first of those takes the earlier lanes' runs when it
+            // entered from them
+            const bool enter = lane > 0 && !b0;
+            sssp_pull_queue(sm, tail, b0 && (lane > 0 || ckey >= 0), kk_s - 1, kk_s - 1 != k_first, in_min);
+            sssp_pull_queue(sm, tail, b1, kk_s, kk_s != k_first, enter ? fminf(s0, in_min) : s0);
+            const int32_t k1 = kk_s + (int32_t)b1;
+            sssp_pull_queue(sm, tail, b2, k1, k1 != k_first, enter && !b1 ? fminf(s1, in_min) : s1);
+            const int32_t k2 = k1 + (int32_t)b2;
+            sssp_pull_queue(sm, tail, b3, k2, k2 != k_first, enter && !b1 && !b2 ? fminf(s2, in_min) : s2);
+            ckey = __shfl_sync(0xffffffffu, kk_e, 31);
+            cmin = __shfl_sync(0xffffffffu, gmin, 31);
+            if (tail - head >= 32u) sssp_pull_drain(a, L, sm, head, tail, 32u, acc);
         }
+        // the chunk's last row: its in-edges may continue in the next chunk
+        sssp_pull_queue(sm, tail, lane == 0 && ckey >= 0, ckey, false, cmin);
+        sssp_pull_drain(a, L, sm, head, tail, 1u, acc);
+    }
+}
+
+// The rows a pull iteration improved (stamp = iteration + 1) as the next push queue.
+__device__ __forceinline__ void sssp_stamp_to_queue(const SsspArgs& a, int32_t L, Stage& st) {
+    const int lane = threadIdx.x & 31;
+    const long long gwarp = (long long)((blockIdx.x * kSsspThreads + threadIdx.x) >> 5);
+    const long long nwarps = (long long)((gridDim.x * kSsspThreads) >> 5);
+    for (long long b = gwarp * 32; b < a.n; b += nwarps * 32) {
+        const int32_t v = (int32_t)b + lane;
+        st.put(v < a.n && a.stamp[v] == L + 1, v);
     }
     st.flush();
 }
@@ -191,7 +383,10 @@ __global__ void __launch_bounds__(kSsspThreads, kOcc) sssp_kernel(SsspArgs a) {
     __shared__ StageBuf stage_mem[kSsspThreads / 32];
     __shared__ unsigned long long lvl[4];
     __shared__ unsigned long long acc_mem[kSsspThreads / 32][4];
+    __shared__ __align__(16) SpullSmem pull_sm[kSsspThreads / 32];
     const int wib = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) < 4) pull_sm[wib].occ[threadIdx.x & 31] = 0u;
+    __syncwarp();
     unsigned long long qv = s_od > 0 ? (((unsigned long long)s_od << 32) | 1ull) : 0ull;
     int dir = a.mode == GBX_DIR_PULL ? GBX_DIR_PULL : GBX_DIR_PUSH;
     int cur = 0;
@@ -209,7 +404,7 @@ __global__ void __launch_bounds__(kSsspThreads, kOcc) sssp_kernel(SsspArgs a) {
         if (dir == GBX_DIR_PUSH)
             sssp_push(a, L, cur, qcount, qedges, st, acc);
         else
-            sssp_pull(a, acc);
+            sssp_pull(a, L, pull_sm[wib], acc);
         // counts: n_new, mf_new (push: from the staged degrees), examined edges
         block_add_counts<kSsspThreads / 32>(acc_mem, acc.n_new, acc.mf, acc.exam, 0ull, &cout->n_new, &cout->mf_new,
                                             &cout->e_exam, nullptr);
@@ -235,7 +430,7 @@ __global__ void __launch_bounds__(kSsspThreads, kOcc) sssp_kernel(SsspArgs a) {
         }
         if (dir == GBX_DIR_PULL && next == GBX_DIR_PUSH) {
             // the improved set becomes the queue (with its degree prefix)
-            sssp_chg_to_queue(a, st);
+            sssp_stamp_to_queue(a, L, st);
             if (!grid_barrier(barc, gridDim.x, bar_round, a.status, a.timeout_ns)) return;
             if (threadIdx.x == 0) lvl[3] = ld_volatile_u64(&cout->q);
             __syncthreads();
@@ -305,10 +500,12 @@ extern "C" gbx_status gbx_sssp(gbx_graph* g, int32_t source, float* dist, const 
     a.in_ptr = G->in_ptr;
     a.in_col = G->in_col;
     a.in_val = G->in_val;
-    a.nz_in = G->nz_in;
+    a.nzr = G->nzr_in;
+    a.nzr_ptr = G->nzr_in_ptr;
+    a.nnzr = G->nnzr_in;
+    a.nnz = (int32_t)G->nnz;
     a.dist = dist;
     a.stamp = w.list;  // n ints
-    a.chg = w.bm[2];
     for (int i = 0; i < 2; ++i) {
         a.q[i] = w.q[i];
         a.qp[i] = w.qp[i];

@@ -67,6 +67,38 @@ __global__ void set_weights_kernel(int64_t m, const int32_t* __restrict__ src, c
     }
 }
 
+__global__ void nzr_ptr_kernel(const int32_t* __restrict__ rows, int32_t count, const int32_t* __restrict__ row_ptr,
+                               int32_t n, int32_t* __restrict__ ptr) {
+    for (int32_t j = blockIdx.x * blockDim.x + threadIdx.x; j <= count; j += gridDim.x * blockDim.x)
+        ptr[j] = row_ptr[j < count ? rows[j] : n];
+}
+
+// The compact list of rows with in-edges and their in-edge starts (Graph::nzr_in).
+static gbx_status build_nzr_in(Graph* G, cudaStream_t s) {
+    int32_t* count_dev = G->ws.flag + 9;
+    GBX_TRY(bitmap_to_list(G->nz_in, G->n, G->ws.list, count_dev, G->ws.qd[0], G->ws.scan_tmp, s));
+    int32_t count = 0;
+    GBX_CUDA_TRY(cudaMemcpyAsync(&count, count_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    GBX_CUDA_TRY(cudaStreamSynchronize(s));
+    int32_t* buf = nullptr;
+    GBX_CUDA_TRY(cudaMalloc((void**)&buf, sizeof(int32_t) * (2 * (size_t)count + 1)));
+    cudaError_t e = cudaMemcpyAsync(buf, G->ws.list, sizeof(int32_t) * (size_t)count, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) {
+        const unsigned grid = div_up((int64_t)count + 1, 256) < 4096u ? div_up((int64_t)count + 1, 256) : 4096u;
+        nzr_ptr_kernel<<<grid, 256, 0, s>>>(buf, count, G->in_ptr, G->n, buf + count);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaFree(buf);
+        GBX_CUDA_TRY(e);
+    }
+    G->nzr_in = buf;
+    G->nzr_in_ptr = buf + count;
+    G->nnzr_in = count;
+    return GBX_OK;
+}
+
 }  // namespace gbx
 
 using namespace gbx;
@@ -98,6 +130,7 @@ extern "C" gbx_status gbx_graph_set_weights(gbx_graph* g, int64_t m, const int32
         G->out_val = ov;
         G->in_val = G->symmetric ? ov : iv;
     }
+    if (!G->nzr_in) GBX_TRY(build_nzr_in(G, s));
     const float inf = INFINITY;
     if (nnz > 0) {
         fill_f32_kernel<<<div_up(nnz, 256) < 4096u ? div_up(nnz, 256) : 4096u, 256, 0, s>>>(G->out_val, nnz, inf);
