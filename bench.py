@@ -616,6 +616,13 @@ def run_ablation(args):
         push_t = per["push"]["time_ns"] / 1e3
         pull_t = per["pull"]["time_ns"] / 1e3
         best = np.minimum(push_t, pull_t)
+        # the ratio-rule thresholds that reproduce the per-level best schedule (what the
+        # autotuner adds to its candidates), and a run with them
+        da, db, _ = gbx.tune_thresholds(per["push"], per["pull"], n)
+        d = gbx.Desc.from_buffer_copy(gbx.desc_init(alpha=da, beta=db, trace=1))
+        gbx.bfs(g, int(s0), depth, parent, d)
+        gbx.bfs(g, int(s0), depth, parent, d)
+        der = gbx.bfs_trace(g)
         levels.append({
             "source": int(s0),
             "frontier": [int(x) for x in per["push"]["nf"]],
@@ -626,7 +633,10 @@ def run_ablation(args):
             "best_schedule": "".join("P" if a <= b else "L" for a, b in zip(push_t, pull_t)),
             "auto_schedule": "".join("P" if x == gbx.DIR_PUSH else "L" for x in per["auto"]["direction"]),
             "best_total_us": round(float(best.sum()), 1),
-            "auto_total_us": round(float(per["auto"]["time_ns"].sum() / 1e3), 1)})
+            "auto_total_us": round(float(per["auto"]["time_ns"].sum() / 1e3), 1),
+            "derived_alpha_beta": [da, db],
+            "derived_schedule": "".join("P" if x == gbx.DIR_PUSH else "L" for x in der["direction"]),
+            "derived_total_us": round(float(der["time_ns"].sum() / 1e3), 1)})
     out = {"metric": "GTEPS (reached undirected edges / time) per cumulative optimisation", "unit": UNIT,
            "graph": {"name": "rmat21-ef48", "vertices": n, "stored_edges": int(nnz), "sources": len(srcs)},
            "ladder": rows, "tuned_descriptor": gbx.desc_dict(tuned), "per_level": levels,

@@ -403,7 +403,9 @@ gbx_status gbx_bfs_batch_trace(gbx_graph* g, gbx_level* levels, int32_t cap, int
  * fastest in *best (and its time in ms in *best_ms, may be NULL).  Section 6.3
  * chose its switch point by comparison with running both directions on every
  * level; here whole descriptors are compared: for GBX_TUNE_BFS the direction
- * rule (ratio / Beamer) x alpha x beta, then the pull probe depth and the
+ * rule (ratio / Beamer) x alpha x beta plus the ratio-rule thresholds that
+ * gbx_tune_thresholds derives from traced push-only and pull-only runs of up
+ * to 8 of the sources, then the pull probe depth and the
  * persistent blocks per SM; for GBX_TUNE_BATCH the batch alpha, then the probe
  * depth; for GBX_TUNE_SSSP alpha x beta (beta 0: two phases), push only and pull
  * only.  Results never change (every candidate computes the same output).  If
@@ -414,6 +416,25 @@ gbx_status gbx_bfs_batch_trace(gbx_graph* g, gbx_level* levels, int32_t cap, int
  */
 gbx_status gbx_autotune(gbx_graph* g, int32_t kind, const int32_t* sources, int32_t count, gbx_desc* best,
                         double* best_ms, const char* cache_path, void* stream);
+
+/*
+ * Section 6.3 set its switch thresholds by comparison with running both
+ * directions on every level.  push and pull are the traces (gbx_bfs_trace, host
+ * arrays of nlevels records) of one source's BFS run with direction GBX_DIR_PUSH
+ * and GBX_DIR_PULL: the same levels, each timed both ways.  The per-level faster
+ * direction is the best schedule (level 0 pushes, as the rule starts), written to
+ * schedule[0 .. nlevels) if schedule is not NULL.  *alpha and *beta receive the
+ * thresholds of the ratio rule (GBX_HEUR_RATIO) that switch where that schedule
+ * switches: to pull at its first pull level, back to push at its first push level
+ * after that, as far as the rule's conditions (frontier grew / shrank) allow.
+ * alpha = 1e30 when the schedule never pulls, beta = 0 when it never returns to
+ * push.  gbx_autotune(GBX_TUNE_BFS) adds these thresholds, from up to 8 of its
+ * sources, to its timed candidates.  Host only, no device work.  Errors:
+ * NULL_POINTER, INVALID_VALUE (nlevels or n < 1, or traces whose level sizes
+ * differ: not one BFS).
+ */
+gbx_status gbx_tune_thresholds(const gbx_level* push, const gbx_level* pull, int32_t nlevels, int32_t n,
+                               float* alpha, float* beta, int32_t* schedule);
 
 /* ------------------------------------------------------------------ server */
 

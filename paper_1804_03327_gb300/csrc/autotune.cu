@@ -3,6 +3,7 @@
 // by comparing against running both directions on every level and choosing the
 // faster; here the candidates are whole descriptors (direction rule, thresholds,
 // lane probe depth, persistent blocks per SM) timed end to end with CUDA events.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -56,9 +57,70 @@ static void cache_store(const char* path, const TuneKey& k, const gbx_desc& d, d
     std::fclose(f);
 }
 
+// Section 6.3's rule (ratio form) decides level L + 1 at the end of level L from
+// r = |F_{L+1}| / n: push -> pull when r > alpha and the frontier grew, pull ->
+// push when r < beta and it shrank.  Returns the thresholds that switch where the
+// per-level best schedule `best` (level 0 pushes) switches, as far as the rule can.
+static void thresholds_for_schedule(const gbx_level* tr, const std::vector<int32_t>& best, int32_t n, float* alpha,
+                                    float* beta) {
+    const int32_t nl = (int32_t)best.size();
+    auto r = [&](int32_t L) { return (double)tr[L].n_new / (double)n; };
+    auto grew = [&](int32_t L) { return tr[L].n_new > tr[L].nf; };
+    auto shrank = [&](int32_t L) { return tr[L].n_new < tr[L].nf; };
+    int32_t lp = -1;
+    for (int32_t L = 1; L < nl && lp < 0; ++L)
+        if (best[L] == GBX_DIR_PULL) lp = L;
+    if (lp < 0) {  // push throughout: never switch
+        *alpha = 1e30f;
+        *beta = 0.0f;
+        return;
+    }
+    // switch at the end of level lp - 1, not at an earlier level whose frontier grew
+    const double hi = r(lp - 1);
+    double lo = 0.0;
+    for (int32_t L = 0; L < lp - 1; ++L)
+        if (grew(L) && r(L) > lo) lo = r(L);
+    double a = hi * 0.5;
+    if (lo > 0.0 && lo < hi) a = std::sqrt(lo * hi);
+    *alpha = (float)a;
+    int32_t lq = -1;
+    for (int32_t L = lp + 1; L < nl && lq < 0; ++L)
+        if (best[L] == GBX_DIR_PUSH) lq = L;
+    if (lq < 0) {  // pull to the end
+        *beta = 0.0f;
+        return;
+    }
+    // back to push at the end of level lq - 1, not at an earlier pull level that shrank
+    const double blo = r(lq - 1);
+    double bhi = 1e300;
+    for (int32_t L = lp; L < lq - 1; ++L)
+        if (shrank(L) && r(L) < bhi) bhi = r(L);
+    double b = blo * 2.0 + 1.0 / (double)n;
+    if (bhi < 1e300 && blo < bhi) b = std::sqrt((blo > 0.0 ? blo : 1.0 / (double)n) * bhi);
+    *beta = (float)b;
+}
+
 }  // namespace gbx
 
 using namespace gbx;
+
+extern "C" gbx_status gbx_tune_thresholds(const gbx_level* push, const gbx_level* pull, int32_t nlevels, int32_t n,
+                                          float* alpha, float* beta, int32_t* schedule) {
+    clear_error();
+    GBX_CHECK(push != nullptr && pull != nullptr && alpha != nullptr && beta != nullptr, GBX_ERR_NULL_POINTER,
+              "push, pull, alpha and beta are required");
+    GBX_CHECK(nlevels >= 1 && n >= 1, GBX_ERR_INVALID_VALUE, "nlevels and n must be >= 1");
+    std::vector<int32_t> best((size_t)nlevels);
+    for (int32_t L = 0; L < nlevels; ++L) {
+        GBX_CHECK(push[L].nf == pull[L].nf && push[L].n_new == pull[L].n_new && push[L].level == L &&
+                      pull[L].level == L,
+                  GBX_ERR_INVALID_VALUE, "the two traces are not the levels of one BFS");
+        best[L] = L > 0 && pull[L].time_ns < push[L].time_ns ? GBX_DIR_PULL : GBX_DIR_PUSH;
+        if (schedule) schedule[L] = best[L];
+    }
+    thresholds_for_schedule(push, best, n, alpha, beta);
+    return GBX_OK;
+}
 
 extern "C" gbx_status gbx_autotune(gbx_graph* g, int32_t kind, const int32_t* sources, int32_t count, gbx_desc* best,
                                    double* best_ms, const char* cache_path, void* stream) {
@@ -173,6 +235,36 @@ extern "C" gbx_status gbx_autotune(gbx_graph* g, int32_t kind, const int32_t* so
     if (ce != cudaSuccess) {
         st = GBX_ERR_CUDA;
         set_error(std::string("cudaEventCreate: ") + cudaGetErrorString(ce));
+    }
+    // Section 6.3 set its thresholds by comparison with running both directions on
+    // every level.  A BFS visits the same levels whichever direction each takes, so
+    // traced push-only and pull-only runs of (up to 8 of) the tuning sources give each
+    // level's cost both ways; the ratio-rule thresholds that reproduce each source's
+    // per-level best schedule join the timed candidates.
+    if (kind == GBX_TUNE_BFS && st == GBX_OK) {
+        std::vector<gbx_level> tp(kTraceCap), tq(kTraceCap);
+        for (int32_t k = 0; k < count && k < 8 && st == GBX_OK; ++k) {
+            int32_t np = 0, nq = 0;
+            gbx_desc dp = base, dq = base;
+            dp.direction = GBX_DIR_PUSH;
+            dq.direction = GBX_DIR_PULL;
+            dp.trace = dq.trace = 1;
+            st = gbx_bfs(g, sources[k], static_cast<int32_t*>(depth), nullptr, &dp, stream);
+            if (st == GBX_OK) st = gbx_bfs_trace(g, tp.data(), kTraceCap, &np);
+            if (st == GBX_OK) st = gbx_bfs(g, sources[k], static_cast<int32_t*>(depth), nullptr, &dq, stream);
+            if (st == GBX_OK) st = gbx_bfs_trace(g, tq.data(), kTraceCap, &nq);
+            if (st != GBX_OK || np != nq || np < 1 || np >= kTraceCap) continue;
+            gbx_desc d = base;
+            d.heuristic = GBX_HEUR_RATIO;
+            if (gbx_tune_thresholds(tp.data(), tq.data(), np, G->n, &d.alpha, &d.beta, nullptr) != GBX_OK) continue;
+            bool seen = false;
+            for (const gbx_desc& c : cand)
+                if (c.heuristic == d.heuristic && std::fabs(c.alpha - d.alpha) <= 0.05f * d.alpha &&
+                    std::fabs(c.beta - d.beta) <= 0.05f * d.beta)
+                    seen = true;
+            if (!seen) cand.push_back(d);
+        }
+        if (st == GBX_OK) clear_error();
     }
     gbx_desc winner = base;
     double win_ms = 1e300;

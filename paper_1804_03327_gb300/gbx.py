@@ -59,6 +59,7 @@ EXPORTED = [
     "gbx_server_config_init", "gbx_server_create", "gbx_server_add_graph", "gbx_server_graph_lanes",
     "gbx_server_submit", "gbx_server_poll", "gbx_server_stats", "gbx_server_destroy", "gbx_autotune",
     "gbx_graph_set_weights", "gbx_graph_copy_weights", "gbx_sssp", "gbx_sssp_trace", "gbx_server_set_graph_desc",
+    "gbx_tune_thresholds",
 ]
 
 
@@ -157,6 +158,9 @@ def load():
                 "gbx_graph_copy_weights": (ctypes.c_int, [p, i32, p]),
                 "gbx_sssp": (ctypes.c_int, [p, i32, p, ctypes.POINTER(Desc), p]),
                 "gbx_sssp_trace": (ctypes.c_int, [p, ctypes.POINTER(Level), i32, ctypes.POINTER(i32)]),
+                "gbx_tune_thresholds": (ctypes.c_int, [ctypes.POINTER(Level), ctypes.POINTER(Level), i32, i32,
+                                                       ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                                                       ctypes.POINTER(i32)]),
             }
             for name, (res, args) in sigs.items():
                 fn = getattr(L, name)
@@ -390,6 +394,24 @@ def autotune(g: Graph, kind: int, sources, cache_path: str | None = None, stream
     _check(load().gbx_autotune(g.handle, int(kind), srcs.ctypes.data, len(srcs), ctypes.byref(d), ctypes.byref(ms),
                                cache_path.encode() if cache_path else None, _stream_ptr(stream)), "gbx_autotune")
     return d, ms.value
+
+
+def tune_thresholds(push_trace: np.ndarray, pull_trace: np.ndarray, n: int):
+    """Ratio-rule (alpha, beta) reproducing the per-level best schedule of one BFS
+    traced both ways (gbx_tune_thresholds), and that schedule."""
+    k = len(push_trace)
+    bufs = []
+    for tr in (push_trace, pull_trace):
+        b = (Level * max(k, 1))()
+        for i in range(min(k, len(tr))):
+            for f in LEVEL_FIELDS:
+                setattr(b[i], f, int(tr[i][f]))
+        bufs.append(b)
+    a, bt = ctypes.c_float(), ctypes.c_float()
+    sched = (ctypes.c_int32 * max(k, 1))()
+    _check(load().gbx_tune_thresholds(bufs[0], bufs[1], k if len(pull_trace) == k else -1, int(n), ctypes.byref(a),
+                                      ctypes.byref(bt), sched), "gbx_tune_thresholds")
+    return a.value, bt.value, [int(x) for x in sched[:k]]
 
 
 def desc_dict(d: Desc) -> dict:
