@@ -51,6 +51,7 @@ struct BfsArgs {
     const uint32_t* nz_in;
     const uint32_t* multi_in;
     const int32_t* first_in;
+    const int4* next_in;
     int32_t* depth;
     int32_t* parent;
     uint32_t* vis[2];
@@ -285,34 +286,40 @@ __device__ __forceinline__ int warp_scan(const int32_t* __restrict__ in_col, con
 }
 
 // A warp takes a tile of a.tile_words bitmap words and finds the rows the mask
-// lets through (unvisited, with in-edges).  Pass 1 tests every such row's first
-// in-neighbour (the dense first_in array) against the frontier, kP1 rows per lane
-// in flight, packed in registers (per-word popcount, warp scan, __fns); most rows
+// lets through (unvisited, with in-edges), listed in shared memory in row order
+// (put_tile_list).  Pass 1 tests every such row's first in-neighbour (the dense
+// first_in array) against the frontier, kP1 rows per lane in flight; most rows
 // of a power-law graph settle here.  Pass 2 takes the rows pass 1 left open that
 // have more in-neighbours, 32 * kPullIlp per round, kPullIlp rows per lane probing
-// in lockstep; rows longer than the probe depth are finished by the whole warp, or
-// by the whole grid when they are very long.
+// in lockstep: in-neighbours 1..4 from the dense next_in array, then the lane
+// probe; rows longer than the probe depth are finished by the whole warp, or by
+// the whole grid when they are very long.
 #ifndef GBX_PULL_P1
 #define GBX_PULL_P1 4
 #endif
 constexpr int kP1 = GBX_PULL_P1;  // pass-1 rows per lane per round
 
-// Word j of a warp's tile holding candidate c of the packed list (excl: exclusive
-// prefix of the words' candidate counts, lane j holding word j's), and c's bit.
-__device__ __forceinline__ int cand_word(uint32_t excl, uint32_t c) {
-    int j = 0;
-#pragma unroll
-    for (int step = 16; step >= 1; step >>= 1) {
-        const uint32_t ev = __shfl_sync(0xffffffffu, excl, j + step);
-        if (ev <= c) j += step;
+// The rows of a tile whose bits are set in the lane words `m` (lane l holds word l
+// of the tile), in row order, as offsets in the tile: the lane writes its word's
+// rows at its exclusive prefix `excl` of the words' bit counts.  One pass over the
+// set bits, where a per-round search of the packed list costs a warp-wide binary
+// search of shuffles and an n-th-set-bit per entry.  The warp syncs before (earlier
+// readers of the list) and after.
+__device__ __forceinline__ void put_tile_list(uint16_t* clist, uint32_t m, uint32_t excl) {
+    __syncwarp();
+    const uint32_t rowbase = (threadIdx.x & 31) << 5;
+    while (m) {
+        const uint32_t b = __ffs(m) - 1;
+        m &= m - 1;
+        clist[excl++] = (uint16_t)(rowbase + b);
     }
-    return j;
+    __syncwarp();
 }
 
 template <bool kHuge>
 __device__ __forceinline__ void pull_level(const BfsArgs& a, int32_t L, int vcur, bool use_fbm, bool append,
                                            const HugeRows& hr, Stage& st, unsigned long long* bsm, uint32_t* snew,
-                                           Acc& acc) {
+                                           uint16_t* clist, Acc& acc) {
     const int lane = threadIdx.x & 31;
     const int gwarp = (int)((blockIdx.x * kBfsThreads + threadIdx.x) >> 5);
     const int nwarps = (int)((gridDim.x * kBfsThreads) >> 5);
@@ -339,26 +346,29 @@ __device__ __forceinline__ void pull_level(const BfsArgs& a, int32_t L, int vcur
         // ---- pass 1: the first in-neighbour of every candidate row
         if (two_pass) {
             const uint32_t total = totalc;
-            const uint32_t excl = inclc - cntc;
+            put_tile_list(clist, cand, inclc - cntc);
             acc.exam += cntc;  // every candidate examines its first in-neighbour
             for (uint32_t base = 0; base < total; base += 32 * kP1) {
                 int32_t i[kP1], f0[kP1];
 #pragma unroll
                 for (int r = 0; r < kP1; ++r) {
                     const uint32_t c = base + 32 * r + lane;
-                    const int j = cand_word(excl, c);
-                    const uint32_t cj = __shfl_sync(0xffffffffu, cand, j);
-                    const uint32_t ej = __shfl_sync(0xffffffffu, excl, j);
-                    i[r] = c < total ? ((tile * tw + j) << 5) + (int)__fns(cj, 0u, (int)(c - ej) + 1) : -1;
+                    i[r] = c < total ? ((tile * tw) << 5) + (int)clist[c] : -1;
                 }
 #pragma unroll
                 for (int r = 0; r < kP1; ++r) f0[r] = i[r] >= 0 ? __ldg(a.first_in + i[r]) : -1;
+                // every probe of the round is loaded before the round's first store: a store to
+                // depth or parent may alias the bitmap as far as the compiler knows, and a load
+                // after it would wait for the one before
+                bool hitr[kP1];
+#pragma unroll
+                for (int r = 0; r < kP1; ++r) hitr[r] = f0[r] >= 0 && bit_test(tbm, f0[r]);
 #pragma unroll
                 for (int r = 0; r < kP1; ++r) {
                     const int j = (i[r] >> 5) - tile * tw;  // word of the tile (any lane when i < 0)
                     const int bp = i[r] & 31;
                     const uint32_t cwj = __shfl_sync(0xffffffffu, cw, j & 31);
-                    const bool hit = f0[r] >= 0 && bit_test(tbm, f0[r]);
+                    const bool hit = hitr[r];
                     if (hit) atomicOr(snew + j, 1u << bp);
                     // without masking a visited row may find a parent too; only unvisited rows are new
                     const bool isnew = hit && !((cwj >> bp) & 1u);
@@ -386,7 +396,7 @@ __device__ __forceinline__ void pull_level(const BfsArgs& a, int32_t L, int vcur
         const uint32_t cntw = __popc(sv);
         const uint32_t incl = warp_inclusive_sum(cntw);
         const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-        const uint32_t excl = incl - cntw;
+        if (total) put_tile_list(clist, sv, incl - cntw);
         for (uint32_t base = 0; base < total; base += 32 * kPullIlp) {
             bool mine[kPullIlp], found[kPullIlp], found1[kPullIlp], done[kPullIlp];
             int jw[kPullIlp], bitpos[kPullIlp];
@@ -397,13 +407,12 @@ __device__ __forceinline__ void pull_level(const BfsArgs& a, int32_t L, int vcur
             for (int r = 0; r < kPullIlp; ++r) {
                 const uint32_t c = base + 32 * r + lane;
                 mine[r] = c < total;
-                const int j = cand_word(excl, c);
+                const int off = mine[r] ? (int)clist[c] : 0;
+                const int j = off >> 5;
                 jw[r] = j;
-                const uint32_t cj = __shfl_sync(0xffffffffu, sv, j);
-                const uint32_t ej = __shfl_sync(0xffffffffu, excl, j);
                 const uint32_t f1j = __shfl_sync(0xffffffffu, f1, j);
                 cwj[r] = __shfl_sync(0xffffffffu, cw, j);
-                bitpos[r] = mine[r] ? (int)__fns(cj, 0u, (int)(c - ej) + 1) : 0;
+                bitpos[r] = off & 31;
                 i[r] = ((tile * tw + j) << 5) + bitpos[r];
                 // only without early exit does pass 2 see rows pass 1 already found
                 found1[r] = mine[r] && ((f1j >> bitpos[r]) & 1u);
@@ -411,11 +420,13 @@ __device__ __forceinline__ void pull_level(const BfsArgs& a, int32_t L, int vcur
                 done[r] = false;
                 exam[r] = 0;
             }
+            int4 nx[kPullIlp];
 #pragma unroll
             for (int r = 0; r < kPullIlp; ++r) {
                 beg[r] = mine[r] ? __ldg(a.in_ptr + i[r]) : 0;
                 end[r] = mine[r] ? __ldg(a.in_ptr + i[r] + 1) : 0;
                 par[r] = (mine[r] && (!two_pass || found1[r])) ? __ldg(a.first_in + i[r]) : -1;
+                nx[r] = mine[r] ? __ldg(a.next_in + i[r]) : make_int4(-1, -1, -1, -1);
             }
 #pragma unroll
             for (int r = 0; r < kPullIlp; ++r) {
@@ -429,6 +440,27 @@ __device__ __forceinline__ void pull_level(const BfsArgs& a, int32_t L, int vcur
                         par[r] = -1;
                     }
                 }
+            }
+            // in-neighbours 1..4 from the dense next-entries array (one 16-byte load, four probes
+            // in flight); the first hit in row order is the parent
+#pragma unroll
+            for (int r = 0; r < kPullIlp; ++r) {
+                if (!mine[r] || done[r]) continue;
+                const bool h0 = nx[r].x >= 0 && bit_test(tbm, nx[r].x);
+                const bool h1 = nx[r].y >= 0 && bit_test(tbm, nx[r].y);
+                const bool h2 = nx[r].z >= 0 && bit_test(tbm, nx[r].z);
+                const bool h3 = nx[r].w >= 0 && bit_test(tbm, nx[r].w);
+                const int nv = (nx[r].x >= 0) + (nx[r].y >= 0) + (nx[r].z >= 0) + (nx[r].w >= 0);
+                const int hit = h0 ? 0 : (h1 ? 1 : (h2 ? 2 : (h3 ? 3 : -1)));
+                if (hit >= 0 && !found[r]) {
+                    found[r] = true;
+                    par[r] = hit == 0 ? nx[r].x : (hit == 1 ? nx[r].y : (hit == 2 ? nx[r].z : nx[r].w));
+                }
+                const bool stop = hit >= 0 && a.early_exit;
+                const int used = stop ? hit + 1 : nv;
+                exam[r] += (unsigned long long)used;
+                k[r] += used;
+                done[r] = stop;
             }
             // lane probes: up to a.probe in-neighbours per row, kPullStep at a time, both rows in lockstep
             for (int it = 0; it < (a.probe + kPullStep - 1) / kPullStep; ++it) {
@@ -797,6 +829,7 @@ __global__ void __launch_bounds__(kBfsThreads, kBfsMinBlocks) bfs_kernel(BfsArgs
 
     __shared__ StageBuf stage_mem[kBfsThreads / 32];
     __shared__ uint32_t tile_new[kBfsThreads / 32][32];
+    __shared__ uint16_t tile_list[kBfsThreads / 32][1024];  // a pull tile's candidate rows (offsets in the tile)
     __shared__ unsigned long long lvl[6];  // counters of the level just finished, read once per block
     __shared__ unsigned long long acc_mem[kBfsThreads / 32][4];  // per-warp counts before the block's atomics
     __shared__ unsigned long long stage_sum[kBfsThreads / 32];   // per-warp queue ranges of a block flush
@@ -850,7 +883,7 @@ __global__ void __launch_bounds__(kBfsThreads, kBfsMinBlocks) bfs_kernel(BfsArgs
             }
             appended = use_fbm;
             pull_level<kHuge>(a, L, vcur, use_fbm, appended, HugeRows{a.q[cur], a.qp[cur], a.qd[cur], a.hfirst}, st,
-                              stage_sum, tile_new[wib], acc);
+                              stage_sum, tile_new[wib], tile_list[wib], acc);
         }
         flush_acc(acc, cout, kTrace, acc_mem);
         if (!grid_barrier(barc, gridDim.x, bar_round, a.status, a.timeout_ns)) return;
@@ -960,6 +993,7 @@ static gbx_status launch_bfs(Graph* G, int32_t source, int32_t* depth, int32_t* 
     a.nz_in = G->nz_in;
     a.multi_in = G->multi_in;
     a.first_in = G->first_in;
+    a.next_in = G->next_in;
     a.depth = depth;
     a.parent = parent;
     a.vis[0] = G->ws.bm[0];

@@ -135,6 +135,10 @@ struct Graph {
     // pull row reads this dense array instead of a random sector of in_col
     int32_t* first_in = nullptr;
     int32_t* first_out = nullptr;
+    // entries 1..4 of each row (-1 past its end), one 16-byte load: a pull row that the
+    // first entry did not settle probes these before it reads the row offsets and in_col
+    int4* next_in = nullptr;
+    int4* next_out = nullptr;
     // binary32 edge weights (gbx_graph_set_weights): out_val[k] belongs to out_col[k],
     // in_val[k] to in_col[k] (aliases out_val when symmetric); NULL until set
     float* out_val = nullptr;
@@ -329,7 +333,7 @@ struct MxvStats {
 
 __global__ void __launch_bounds__(kMxvThreads)
     mxv_pull_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col, const int32_t* __restrict__ first,
-                    const uint32_t* __restrict__ nzrows, const uint32_t* __restrict__ multi,
+                    const int4* __restrict__ next, const uint32_t* __restrict__ nzrows, const uint32_t* __restrict__ multi,
                     const uint32_t* __restrict__ ubm,
                     const uint32_t* __restrict__ pass, uint32_t* __restrict__ R, int32_t nwords, int early_exit,
                     const int32_t* flag, MxvStats* stats, int32_t* huge, int32_t* huge_next, int32_t* huge_count);

@@ -76,6 +76,16 @@ __global__ void first_neighbour_kernel(const int32_t* __restrict__ row_ptr, cons
         first[i] = row_ptr[i + 1] > row_ptr[i] ? col[row_ptr[i]] : -1;
 }
 
+// next[i] = entries 1..4 of row i (-1 past the row's end).
+__global__ void next_neighbours_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                       int32_t n, int4* __restrict__ next) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t b = row_ptr[i], d = row_ptr[i + 1] - b;
+        next[i] = make_int4(d > 1 ? col[b + 1] : -1, d > 2 ? col[b + 2] : -1, d > 3 ? col[b + 3] : -1,
+                            d > 4 ? col[b + 4] : -1);
+    }
+}
+
 // bm bit i set iff row i has at least min_len entries.
 __global__ void nonzero_rows_kernel(const int32_t* __restrict__ row_ptr, int32_t n, int32_t min_len,
                                     uint32_t* __restrict__ bm) {
@@ -184,6 +194,8 @@ static void graph_release(Graph* g) {
     if (g->nz_out != g->nz_in) f(g->nz_out);
     if (g->first_out != g->first_in) f(g->first_out);
     f(g->first_in);
+    if (g->next_out != g->next_in) f(g->next_out);
+    f(g->next_in);
     if (g->in_val != g->out_val) f(g->in_val);
     f(g->out_val);
     f(g->nzr_in);
@@ -324,6 +336,14 @@ static gbx_status build_impl(Graph* g, int32_t n, int64_t m, const int32_t* src,
     } else {
         GBX_CUDA_TRY(cudaMalloc((void**)&g->first_out, sizeof(int32_t) * ((size_t)n + 1)));
         first_neighbour_kernel<<<grid_for(n), 256, 0, s>>>(g->out_ptr, g->out_col, n, g->first_out);
+    }
+    GBX_CUDA_TRY(cudaMalloc((void**)&g->next_in, sizeof(int4) * ((size_t)n + 1)));
+    next_neighbours_kernel<<<grid_for(n), 256, 0, s>>>(g->in_ptr, g->in_col, n, g->next_in);
+    if (sym) {
+        g->next_out = g->next_in;
+    } else {
+        GBX_CUDA_TRY(cudaMalloc((void**)&g->next_out, sizeof(int4) * ((size_t)n + 1)));
+        next_neighbours_kernel<<<grid_for(n), 256, 0, s>>>(g->out_ptr, g->out_col, n, g->next_out);
     }
     GBX_CUDA_TRY(cudaGetLastError());
     GBX_CUDA_TRY(cudaStreamSynchronize(s));

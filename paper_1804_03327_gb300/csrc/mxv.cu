@@ -27,18 +27,34 @@ constexpr int kMxvChunk = 1024;
 __device__ __forceinline__ bool dir_enabled(const int32_t* flag, int want) { return !flag || *flag == want; }
 
 // Row-based matvec over the rows the mask lets through (Eq 2 / Eq 4).  A warp
-// takes a tile of 32 result words (1024 rows), packs the passing nonempty rows
-// in registers (popcount, warp scan, __fns) and computes them 64 per round, two
-// rows per lane probing in lockstep: the first entry of a row comes from the
-// dense first-entry array when one is given (one coalesced read instead of a
-// random sector), then up to kMxvProbe entries four at a time; longer rows are
-// finished by the whole warp 32 entries at a time.  With early exit a row stops
-// at its first hit (Section 5.3); the result is the same either way.
+// takes a tile of 32 result words (1024 rows), lists the passing nonempty rows in
+// shared memory (each lane its word's rows, at its prefix of the words' counts)
+// and computes them 64 per round, two rows per lane probing in lockstep: the
+// first entry of a row comes from the dense first-entry array when one is given
+// (one coalesced read instead of a random sector), entries 1..4 from the dense
+// next-entries array (one 16-byte read), then up to kMxvProbe entries four at a
+// time; longer rows are finished by the whole warp 32 entries at a time.  With
+// early exit a row stops at its first hit (Section 5.3); the result is the same
+// either way.
 constexpr int kMxvIlp = 2;
 constexpr int kMxvP1 = 4;  // first-pass rows per lane per round
 
+// The rows of a tile whose bits are set in the lane words m (lane l: word l), in
+// row order, as offsets in the tile, written at the lane's prefix excl.
+__device__ __forceinline__ void mxv_tile_list(uint16_t* list, uint32_t m, uint32_t excl) {
+    __syncwarp();
+    const uint32_t rowbase = (threadIdx.x & 31) << 5;
+    while (m) {
+        const uint32_t b = __ffs(m) - 1;
+        m &= m - 1;
+        list[excl++] = (uint16_t)(rowbase + b);
+    }
+    __syncwarp();
+}
+
 __global__ void __launch_bounds__(kMxvThreads) mxv_pull_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
                                                                 const int32_t* __restrict__ first,
+                                                                const int4* __restrict__ next,
                                                                 const uint32_t* __restrict__ nzrows,
                                                                 const uint32_t* __restrict__ multi,
                                                                 const uint32_t* __restrict__ ubm,
@@ -48,7 +64,9 @@ __global__ void __launch_bounds__(kMxvThreads) mxv_pull_kernel(const int32_t* __
                                                                 int32_t* huge_count) {
     if (!dir_enabled(flag, GBX_DIR_PULL)) return;
     __shared__ uint32_t tile_hits[kMxvThreads / 32][32];
+    __shared__ uint16_t tile_rows[kMxvThreads / 32][1024];
     uint32_t* hits = tile_hits[threadIdx.x >> 5];
+    uint16_t* list = tile_rows[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
@@ -68,21 +86,13 @@ __global__ void __launch_bounds__(kMxvThreads) mxv_pull_kernel(const int32_t* __
         const uint32_t total0 = __shfl_sync(0xffffffffu, incl0, 31);
         const bool two_pass = first != nullptr && total0 > 32u * kMxvIlp;
         if (two_pass) {
-            const uint32_t excl0 = incl0 - cnt0;
+            mxv_tile_list(list, cand0, incl0 - cnt0);
             for (uint32_t base = 0; base < total0; base += 32 * kMxvP1) {
                 int32_t i[kMxvP1], f0[kMxvP1];
 #pragma unroll
                 for (int r = 0; r < kMxvP1; ++r) {
                     const uint32_t c = base + 32 * r + lane;
-                    int j = 0;
-#pragma unroll
-                    for (int step = 16; step >= 1; step >>= 1) {
-                        const uint32_t ev = __shfl_sync(0xffffffffu, excl0, j + step);
-                        if (ev <= c) j += step;
-                    }
-                    const uint32_t cj = __shfl_sync(0xffffffffu, cand0, j);
-                    const uint32_t ej = __shfl_sync(0xffffffffu, excl0, j);
-                    i[r] = c < total0 ? (((tile << 5) + j) << 5) + (int)__fns(cj, 0u, (int)(c - ej) + 1) : -1;
+                    i[r] = c < total0 ? (tile << 10) + (int)list[c] : -1;
                 }
 #pragma unroll
                 for (int r = 0; r < kMxvP1; ++r) f0[r] = i[r] >= 0 ? first[i[r]] : -1;
@@ -102,7 +112,7 @@ __global__ void __launch_bounds__(kMxvThreads) mxv_pull_kernel(const int32_t* __
         const uint32_t cntw = __popc(cand);
         const uint32_t incl = warp_inclusive_sum(cntw);
         const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-        const uint32_t excl = incl - cntw;
+        if (total) mxv_tile_list(list, cand, incl - cntw);
         for (uint32_t base = 0; base < total; base += 32 * kMxvIlp) {
             bool mine[kMxvIlp], found[kMxvIlp], done[kMxvIlp];
             int jw[kMxvIlp], bitpos[kMxvIlp];
@@ -112,26 +122,22 @@ __global__ void __launch_bounds__(kMxvThreads) mxv_pull_kernel(const int32_t* __
             for (int r = 0; r < kMxvIlp; ++r) {
                 const uint32_t c = base + 32 * r + lane;
                 mine[r] = c < total;
-                int j = 0;
-#pragma unroll
-                for (int step = 16; step >= 1; step >>= 1) {
-                    const uint32_t ev = __shfl_sync(0xffffffffu, excl, j + step);
-                    if (ev <= c) j += step;
-                }
+                const int off = mine[r] ? (int)list[c] : 0;
+                const int j = off >> 5;
                 jw[r] = j;
-                const uint32_t cj = __shfl_sync(0xffffffffu, cand, j);
-                const uint32_t ej = __shfl_sync(0xffffffffu, excl, j);
                 f1w[r] = __shfl_sync(0xffffffffu, f1, j);
-                bitpos[r] = mine[r] ? (int)__fns(cj, 0u, (int)(c - ej) + 1) : 0;
+                bitpos[r] = off & 31;
                 found[r] = false;
                 done[r] = false;
             }
+            int4 nx[kMxvIlp];
 #pragma unroll
             for (int r = 0; r < kMxvIlp; ++r) {
                 const int32_t i = (((tile << 5) + jw[r]) << 5) + bitpos[r];
                 beg[r] = mine[r] ? ptr[i] : 0;
                 end[r] = mine[r] ? ptr[i + 1] : 0;
                 f0[r] = (mine[r] && !two_pass) ? (first ? first[i] : -2) : -1;
+                nx[r] = (mine[r] && next) ? next[i] : make_int4(-1, -1, -1, -1);
             }
 #pragma unroll
             for (int r = 0; r < kMxvIlp; ++r) {
@@ -148,6 +154,23 @@ __global__ void __launch_bounds__(kMxvThreads) mxv_pull_kernel(const int32_t* __
                     found[r] = true;
                     done[r] = early_exit != 0;
                 }
+            }
+            // entries 1..4 from the dense next-entries array (one 16-byte read, four probes in flight)
+#pragma unroll
+            for (int r = 0; r < kMxvIlp; ++r) {
+                if (!mine[r] || done[r] || !next) continue;
+                const bool h0 = nx[r].x >= 0 && bit_test(ubm, nx[r].x);
+                const bool h1 = nx[r].y >= 0 && bit_test(ubm, nx[r].y);
+                const bool h2 = nx[r].z >= 0 && bit_test(ubm, nx[r].z);
+                const bool h3 = nx[r].w >= 0 && bit_test(ubm, nx[r].w);
+                const int nv = (nx[r].x >= 0) + (nx[r].y >= 0) + (nx[r].z >= 0) + (nx[r].w >= 0);
+                const int hit = h0 ? 0 : (h1 ? 1 : (h2 ? 2 : (h3 ? 3 : -1)));
+                if (hit >= 0) found[r] = true;
+                const bool stop = hit >= 0 && early_exit;
+                const int used = stop ? hit + 1 : nv;
+                exam += (unsigned long long)used;
+                k[r] += used;
+                done[r] = stop;
             }
             // a lane scans rows of up to kMxvLaneRow entries itself; longer rows get kMxvProbe
             // entries here and the rest from the whole warp below
@@ -491,6 +514,7 @@ gbx_status mxv_issue(Graph* G, gbx_vector* w, const gbx_vector* mask, int32_t se
     const int32_t* pull_col = d.transpose ? G->in_col : G->out_col;
     const uint32_t* pull_nz = d.transpose ? G->nz_in : G->nz_out;
     const int32_t* pull_first = d.transpose ? G->first_in : G->first_out;
+    const int4* pull_next = d.transpose ? G->next_in : G->next_out;
     const int32_t* push_ptr = d.transpose ? G->out_ptr : G->in_ptr;
     const int32_t* push_col = d.transpose ? G->out_col : G->in_col;
 
@@ -576,7 +600,7 @@ gbx_status mxv_issue(Graph* G, gbx_vector* w, const gbx_vector* mask, int32_t se
             int32_t* huge_next = G->ws.qp[1];
             int32_t* huge_count = G->ws.flag + 2;
             GBX_CUDA_TRY(cudaMemsetAsync(huge_count, 0, sizeof(int32_t), s));
-            mxv_pull_kernel<<<G->num_sms * 8, kMxvThreads, 0, s>>>(pull_ptr, pull_col, pull_first, pull_nz,
+            mxv_pull_kernel<<<G->num_sms * 8, kMxvThreads, 0, s>>>(pull_ptr, pull_col, pull_first, pull_next, pull_nz,
                                                                     d.transpose ? G->multi_in : G->multi_out, ubm,
                                                                     pass_bm, R, G->nwords, d.early_exit ? 1 : 0, flag,
                                                                     stats, huge, huge_next, huge_count);

@@ -100,7 +100,7 @@ extern "C" gbx_status gbx_mxv_pull_noalloc(int32_t n, const int32_t* row_ptr, co
         if (mask) GBX_TRY(pack_dense_to_bitmap(mask, n, mask_complement ? 1u : 0u, pass, s));
         const int64_t nw32 = ((int64_t)n + 31) & ~(int64_t)31;
         noalloc_nonempty_rows_kernel<<<div_up(nw32, 256), 256, 0, s>>>(row_ptr, n, nzrows);
-        mxv_pull_kernel<<<sms * 8, kMxvThreads, 0, s>>>(row_ptr, col, nullptr, nzrows, nullptr, ubm, mask ? pass : nullptr, R, nwords,
+        mxv_pull_kernel<<<sms * 8, kMxvThreads, 0, s>>>(row_ptr, col, nullptr, nullptr, nzrows, nullptr, ubm, mask ? pass : nullptr, R, nwords,
                                                 early_exit ? 1 : 0, nullptr, nullptr, nullptr, nullptr, nullptr);
     }
     GBX_TRY(bitmap_to_dense(R, n, nullptr, w, s));
