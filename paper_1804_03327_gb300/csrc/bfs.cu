@@ -89,9 +89,9 @@ __device__ __forceinline__ void flush_acc(const Acc& acc, LevelCtr* cout, bool w
 // waits for any of them, so a step costs about one memory round trip instead of
 // four dependent ones.
 #ifndef GBX_BFS_PUSH_ILP
-#define GBX_BFS_PUSH_ILP 1
+#define GBX_BFS_PUSH_ILP 2
 #endif
-constexpr int kBfsIlp = GBX_BFS_PUSH_ILP;  // edges per lane and step (2 needs more than the 64 registers)
+constexpr int kBfsIlp = GBX_BFS_PUSH_ILP;  // edges per lane and step
 constexpr int kBfsStep = 32 * kBfsIlp;
 // stamp: write depth and parent of the claimed children (level 0 leaves them to the
 // start of level 1, when the concurrently initialised outputs are complete).
@@ -167,8 +167,12 @@ __device__ __forceinline__ void push_level(const BfsArgs& a, int32_t L, int cur,
             for (int t = 0; t < kBfsIlp; ++t) c1[t] = u1[t] >= 0 ? __ldg(a.out_col + b1 + 32 * t + lane + d1[t]) : 0;
             // stage 1 (step it): queue entries
             int32_t u0[kBfsIlp], d0[kBfsIlp];
-            if (it < nsteps) {
-                cur_.map(q, qp, qd, qcount, e0 + it * kBfsStep, e1, u0, d0);
+            if (it == 0) {
+                cur_.map(q, qp, qd, qcount, e0, e1, u0, d0);
+            } else if (it < nsteps) {
+                const int32_t ul = __shfl_sync(0xffffffffu, u1[kBfsIlp - 1], 31);
+                const int32_t dl = __shfl_sync(0xffffffffu, d1[kBfsIlp - 1], 31);
+                cur_.map_after(q, qp, qd, qcount, e0 + it * kBfsStep, e1, ul, dl, u0, d0);
             } else {
 #pragma unroll
                 for (int t = 0; t < kBfsIlp; ++t) {

@@ -321,6 +321,44 @@ struct PushCursorT {
         k += (int32_t)before;
     }
 
+    // As map, for the step right after another step of the same walk whose last
+    // slot (lane 31, slot I - 1) held entry values (u_last, d_last): a step with no
+    // entry boundary in it belongs wholly to that entry and needs no loads (the
+    // heavy push levels of a power-law graph walk a few long rows).
+    __device__ __forceinline__ void map_after(const int32_t* q, const int32_t* qp, const int32_t* qd, uint32_t qcount,
+                                              int32_t base, int32_t e1, int32_t u_last, int32_t d_last,
+                                              int32_t (&u)[I], int32_t (&d)[I]) {
+        const int lane = threadIdx.x & 31;
+        uint32_t occ[I];
+        occupancy(qp, qcount, base, occ);
+        uint32_t any = 0u;
+#pragma unroll
+        for (int t = 0; t < I; ++t) any |= occ[t];
+        if (any == 0u) {
+#pragma unroll
+            for (int t = 0; t < I; ++t) {
+                const bool ok = base + 32 * t + lane < e1;
+                u[t] = ok ? u_last : -1;
+                d[t] = ok ? d_last : 0;
+            }
+            return;
+        }
+        uint32_t before = 0;
+#pragma unroll
+        for (int t = 0; t < I; ++t) {
+            const int32_t kk = k + (int32_t)(before + __popc(occ[t] & (0xffffffffu >> (31 - lane))));
+            before += __popc(occ[t]);
+            const int32_t e = base + 32 * t + lane;
+            u[t] = -1;
+            d[t] = 0;
+            if (e < e1) {
+                u[t] = q[kk];
+                d[t] = qd[kk];
+            }
+        }
+        k += (int32_t)before;
+    }
+
     // The entry of each lane's edge slots of the step [base, base + kStep) (qp must
     // be strictly ascending: no entry without edges); the cursor moves on to the
     // entry of the step's last edge.  A slot at or past the end of the last entry's

@@ -122,7 +122,13 @@ __device__ __forceinline__ void sssp_push(const SsspArgs& a, int32_t L, int cur,
             }
             // stage 1 (step it): queue entries
             int32_t u0[1] = {-1}, d0[1] = {0};
-            if (it < nsteps) cur_.map(q, qp, qd, qcount, e0 + it * 32, e1, u0, d0);
+            if (it == 0) {
+                cur_.map(q, qp, qd, qcount, e0, e1, u0, d0);
+            } else if (it < nsteps) {
+                const int32_t ul = __shfl_sync(0xffffffffu, u1, 31);
+                const int32_t dl = __shfl_sync(0xffffffffu, d1, 31);
+                cur_.map_after(q, qp, qd, qcount, e0 + it * 32, e1, ul, dl, u0, d0);
+            }
             // stage 5, continued: queue the claimed children
             const bool queued = lowered && prev < L + 1;
             acc.exam += u1 >= 0 ? 1u : 0u;
