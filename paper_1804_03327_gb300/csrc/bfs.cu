@@ -107,7 +107,9 @@ __device__ __forceinline__ void push_level(const BfsArgs& a, int32_t L, int cur,
     uint32_t* vis = a.vis[vcur];
     const int32_t E = (int32_t)qedges;
     int32_t chunk = (int32_t)(((long long)E + nwarps - 1) / nwarps);
-    chunk = chunk < kBfsStep ? kBfsStep : ((chunk + kBfsStep - 1) / kBfsStep) * kBfsStep;
+    // a level with at most 32 edges per warp gives each warp 32 (one slot of a step filled):
+    // twice the warps of full steps, each with a single step's round trips
+    chunk = chunk <= 32 ? 32 : ((chunk + kBfsStep - 1) / kBfsStep) * kBfsStep;
     for (long long e0l = (long long)gwarp * chunk; e0l < E; e0l += (long long)nwarps * chunk) {
         const int32_t e0 = (int32_t)e0l;
         const int32_t e1 = E - e0 > chunk ? e0 + chunk : E;
@@ -119,11 +121,19 @@ __device__ __forceinline__ void push_level(const BfsArgs& a, int32_t L, int cur,
             // a single step (a small frontier): no pipeline fill and drain
             for (int32_t base = e0; base < e1; base += kBfsStep) {
                 const PushStepT<kBfsIlp> now = cur_.gather(a.out_col, q, qp, qd, qcount, base, e1);
+                // every slot's probe, then every slot's claim: the slots' round trips overlap
+                uint32_t w[kBfsIlp], old[kBfsIlp];
+#pragma unroll
+                for (int t = 0; t < kBfsIlp; ++t) w[t] = now.u[t] >= 0 ? __ldca(vis + (now.v[t] >> 5)) : 0xffffffffu;
 #pragma unroll
                 for (int t = 0; t < kBfsIlp; ++t) {
                     const uint32_t bit = 1u << (now.v[t] & 31);
-                    const bool claimed = now.u[t] >= 0 && !(__ldca(vis + (now.v[t] >> 5)) & bit) &&
-                                         !(atomicOr(vis + (now.v[t] >> 5), bit) & bit);
+                    old[t] = (now.u[t] >= 0 && !(w[t] & bit)) ? atomicOr(vis + (now.v[t] >> 5), bit) : 0xffffffffu;
+                }
+#pragma unroll
+                for (int t = 0; t < kBfsIlp; ++t) {
+                    const uint32_t bit = 1u << (now.v[t] & 31);
+                    const bool claimed = now.u[t] >= 0 && !(old[t] & bit);
                     if (claimed) {
                         if (stamp) {
                             a.depth[now.v[t]] = L + 1;
