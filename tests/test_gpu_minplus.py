@@ -188,3 +188,46 @@ def test_sssp_isolated_source_and_bad_arguments():
     with pytest.raises(gbx.GbxError) as e:
         gbx.sssp(g, 0, dist, gbx.desc_init(push_sort=1))
     assert e.value.status == gbx.ERR_NOT_SUPPORTED
+
+
+def _pull_shape(shape):
+    """Graphs whose in-edge lists cut across the pull's equal per-warp chunks in every way: a hub
+    row spanning many chunks, long runs of one-edge rows (rows ending at lane and chunk borders),
+    and rows with in-edges interleaved with many rows without any."""
+    rng = np.random.default_rng(81)
+    if shape == "star":  # vertex 0 is every other vertex's neighbour, plus a weighted path
+        n = 20001
+        s = np.concatenate([np.arange(1, n), np.arange(1, n - 1)])
+        d = np.concatenate([np.zeros(n - 1, np.int64), np.arange(2, n)])
+        return n, s, d, True
+    if shape == "cycle":  # directed: every row has exactly one in-edge, n iterations deep
+        n = 2000
+        s = np.arange(n)
+        return n, s, (s + 1) % n, False
+    # mixed: sparse random edges on a third of the vertices, a hub to 4000 of them, the rest isolated
+    n = 30000
+    live = rng.choice(n, n // 3, replace=False)
+    s = live[rng.integers(0, len(live), 3 * len(live))]
+    d = live[rng.integers(0, len(live), 3 * len(live))]
+    hub = int(live[0])
+    fan = live[rng.choice(len(live), 4000, replace=False)]
+    return n, np.concatenate([s, np.full(len(fan), hub)]), np.concatenate([d, fan]), True
+
+
+@pytest.mark.parametrize("shape", ["star", "cycle", "mixed"])
+def test_sssp_pull_chunk_borders(shape):
+    n, s, d, sym = _pull_shape(shape)
+    w = weights(len(s), 82, True)
+    og = oracle.graph_weighted(n, s, d, w, symmetrize=sym)
+    g = gbx.graph_build(n, s, d, symmetrize=sym)
+    gbx.graph_set_weights(g, s, d, w)
+    dist = torch.zeros(n, dtype=torch.float32, device="cuda")
+    srcs = [0, 1, n // 2] if shape != "mixed" else [int(x) for x in synth.sources(n, s, d, 3, seed=8)]
+    for src in srcs:
+        want, _ = oracle.sssp(og, src)
+        for desc in [gbx.desc_init(direction=gbx.DIR_PULL), gbx.desc_init(), gbx.desc_init(direction=gbx.DIR_PUSH),
+                     gbx.desc_init(alpha=0.2, beta=0.3)]:
+            gbx.sssp(g, src, dist, desc)
+            gbx.graph_sync(g)
+            assert np.array_equal(dist.cpu().numpy(), want), (shape, src, desc.direction, desc.alpha)
+    g.free()
