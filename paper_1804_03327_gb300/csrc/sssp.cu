@@ -298,6 +298,7 @@ __device__ __forceinline__ void sssp_pull(const SsspArgs& a, int32_t L, SpullSme
             const uint4 o4 = *reinterpret_cast<const uint4*>(sm.occ);
             __syncwarp();
             if (lane < 4) sm.occ[lane] = 0u;
+            __syncwarp();  // the words are clear before any lane's next step sets bits in them
             const uint32_t p0 = __popc(o4.x), p1 = __popc(o4.y), p2 = __popc(o4.z), p3 = __popc(o4.w);
             cur_.k = k0 + (int32_t)(p0 + p1 + p2 + p3);
             // this lane's edges es .. es + 3: where rows start among them, the rows before them
